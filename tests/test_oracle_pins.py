@@ -1,0 +1,384 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against the paper's printed Example 1, exact
+rational arithmetic, a closed form, a textbook property or one of the paper's
+theorems -- never against a re-typed copy of the oracle's own formula.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import laker_oracle as O
+from paper_2604_25138_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _example1():
+    with open(os.path.join(GOLDEN, "example1.json")) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# Example 1 (Sec. IV-E): the paper's worked numbers
+# --------------------------------------------------------------------------
+
+def test_example1_kernel_matches_printed_values():
+    ex = _example1()
+    E = np.array(ex["embeddings"])
+    G = O.kernel_matrix(E, ex["scale"])
+    # embeddings are printed to 3 decimals, G too: G_22 evaluates to 1.134
+    # against the printed 1.133, so 2e-3 absolute is the honest bound.
+    np.testing.assert_allclose(G, np.array(ex["G"]), atol=2e-3, rtol=0)
+    A = O.system_matrix(E, ex["scale"], ex["lambda"])
+    np.testing.assert_allclose(A, np.array(ex["lambda_I_plus_G"]), atol=2e-3, rtol=0)
+
+
+def test_example1_alpha_and_prediction():
+    ex = _example1()
+    E = np.array(ex["embeddings"])
+    y = np.array(ex["y_dbm"])
+    A = O.system_matrix(E, ex["scale"], ex["lambda"])
+    a_direct = O.solve_direct(A, y)
+    a_print = np.array(ex["alpha"])
+    rel = np.linalg.norm(a_direct - a_print) / np.linalg.norm(a_print)
+    assert rel < 2e-3, rel
+    res = O.pcg(A, y, None, tol=1e-14)
+    assert res.converged and res.iterations <= 4
+    np.testing.assert_allclose(res.alpha, a_direct, rtol=1e-10, atol=1e-10)
+    eq = np.array([ex["query_embedding"]])
+    row = O.kernel_matrix(eq, ex["scale"], E)[0]
+    np.testing.assert_allclose(row, np.array(ex["query_kernel_row"]), atol=1e-3, rtol=0)
+    pred = O.radio_map(eq, E, a_direct, ex["scale"])[0]
+    assert abs(pred - ex["query_prediction_dbm"]) < 0.05, pred
+
+
+# --------------------------------------------------------------------------
+# Kernel: closed forms independent of np.exp
+# --------------------------------------------------------------------------
+
+def test_kernel_equals_hadamard_power_series():
+    """exp of a matrix elementwise = sum_m (S)^{o m} / m! (Hadamard powers)."""
+    rng = np.random.default_rng(3)
+    E = rng.normal(size=(13, 5)) * 0.4
+    s = 0.7
+    S = s * (E @ E.T)
+    acc = np.zeros_like(S)
+    term = np.ones_like(S)
+    for m in range(0, 40):
+        acc += term
+        term = term * S / (m + 1)
+    np.testing.assert_allclose(O.kernel_matrix(E, s), acc, rtol=1e-14, atol=0)
+
+
+def test_kernel_zero_embedding_is_all_ones():
+    G = O.kernel_matrix(np.zeros((7, 3)), 1.0)
+    assert np.array_equal(G, np.ones((7, 7)))
+
+
+def test_system_is_spd_and_calibrated_n512():
+    inst = synth.make_instance(512, 16, 1e-3, seed=11, grid=4)
+    G = O.kernel_matrix(inst.Q, inst.scale)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    assert np.array_equal(A, A.T)
+    assert (G > 0).all()
+    w = np.linalg.eigvalsh(A)
+    # Schur product theorem: G = exp(S) elementwise is PSD, so
+    # lambda_min(A) >= lambda.
+    assert w[0] >= inst.lam * (1 - 1e-9)
+    # Sec. III-B: kappa ~ 1 + n/(Q lambda) for one cluster of unit entries;
+    # with entries of mean m the top eigenvalue is ~ n m.
+    approx = 1 + 512 * G.mean() / inst.lam
+    kappa = w[-1] / w[0]
+    assert 0.3 * approx < kappa < 3.0 * approx
+
+
+# --------------------------------------------------------------------------
+# Solve: exact rational brute force and limits
+# --------------------------------------------------------------------------
+
+def _exact_solve(A, y):
+    n = len(y)
+    M = [[Fraction(float(A[i, j])) for j in range(n)] + [Fraction(float(y[i]))] for i in range(n)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    return np.array([float(M[i][n] / M[i][i]) for i in range(n)])
+
+
+@pytest.mark.parametrize("n,lam", [(1, 0.5), (2, 1e-2), (5, 1e-3), (8, 1e-1), (8, 1e-4)])
+def test_solve_matches_exact_rational_arithmetic(n, lam):
+    rng = np.random.default_rng(100 + n)
+    E = rng.normal(size=(n, 3)) * 0.5
+    y = rng.normal(size=n)
+    A = O.system_matrix(E, 1.0, lam)
+    exact = _exact_solve(A, y)
+    scale = np.linalg.norm(exact)
+    assert np.linalg.norm(O.solve_direct(A, y) - exact) / scale < 1e-10
+    for P in (None, O.jacobi_preconditioner(A)):
+        res = O.pcg(A, y, P, tol=1e-14, max_iter=200)
+        assert np.linalg.norm(res.alpha - exact) / scale < 1e-8
+
+
+def test_large_lambda_limit():
+    """alpha -> y / lambda as lambda grows, with |lambda alpha - y| = O(|G|/lambda)."""
+    inst = synth.make_instance(64, 8, 1.0, seed=5, grid=2)
+    G = O.kernel_matrix(inst.Q, inst.scale)
+    gnorm = np.linalg.norm(G, 2)
+    errs = []
+    for lam in (1e4, 1e6):
+        A = G + lam * np.eye(64)
+        a = O.solve_direct(A, inst.y)
+        e = np.linalg.norm(lam * a - inst.y) / np.linalg.norm(inst.y)
+        assert e <= 1.01 * gnorm / lam
+        errs.append(e)
+    assert errs[1] < errs[0] / 50
+
+
+# --------------------------------------------------------------------------
+# PCG: textbook properties
+# --------------------------------------------------------------------------
+
+def _spd_with_spectrum(eigs, seed):
+    rng = np.random.default_rng(seed)
+    V, _ = np.linalg.qr(rng.normal(size=(len(eigs), len(eigs))))
+    return (V * np.asarray(eigs)) @ V.T, V
+
+
+def test_cg_terminates_in_number_of_distinct_eigenvalues():
+    eigs = [1.0] * 10 + [7.0] * 10 + [40.0] * 10
+    A, _ = _spd_with_spectrum(eigs, 1)
+    y = np.random.default_rng(2).normal(size=30)
+    res = O.pcg(A, y, None, tol=1e-11)
+    assert res.converged and res.iterations == 3
+    np.testing.assert_allclose(A @ res.alpha, y, atol=1e-9)
+
+
+def test_pcg_with_exact_inverse_takes_one_iteration():
+    A, _ = _spd_with_spectrum(np.linspace(0.01, 50.0, 20), 4)
+    y = np.random.default_rng(5).normal(size=20)
+    res = O.pcg(A, y, np.linalg.inv(A), tol=1e-10)
+    assert res.iterations == 1
+
+
+def test_pcg_two_distinct_preconditioned_eigenvalues():
+    """If P A has two distinct eigenvalues, PCG stops after two products."""
+    A, V = _spd_with_spectrum(np.linspace(1.0, 1000.0, 24), 6)
+    target = np.array([1.0] * 12 + [3.0] * 12)
+    # P = V diag(target / eig(A)) V^T so that P A = V diag(target) V^T
+    P = (V * (target / np.linspace(1.0, 1000.0, 24))) @ V.T
+    y = np.random.default_rng(7).normal(size=24)
+    res = O.pcg(A, y, P, tol=1e-10)
+    assert res.iterations == 2
+
+
+def test_pcg_matches_direct_within_condition_bound():
+    inst = synth.make_instance(256, 16, 1e-3, seed=9, grid=2)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    a_star = O.solve_direct(A, inst.y)
+    kappa = O.condition_number(A)
+    for P in (None, O.jacobi_preconditioner(A)):
+        res = O.pcg(A, inst.y, P, tol=1e-12)
+        assert res.converged
+        err = np.linalg.norm(res.alpha - a_star) / np.linalg.norm(a_star)
+        assert err <= kappa * 1e-12 * 10
+
+
+# --------------------------------------------------------------------------
+# CCCP: Theorem 1, Tyler's fixed point, stationarity of the MLE objective
+# --------------------------------------------------------------------------
+
+def _ubar(n, n_r, seed):
+    inst = synth.make_instance(n, 6, 1e-2, seed=seed, grid=2)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    return O.random_directions(A, synth.directions(n, n_r, seed)), A
+
+
+def test_random_directions_are_unit_columns_along_A_z():
+    U, A = _ubar(20, 7, 1)
+    Z = synth.directions(20, 7, 1)
+    np.testing.assert_allclose(np.linalg.norm(U, axis=0), 1.0, rtol=1e-14)
+    for k in range(7):
+        # u_k is parallel to A z_k with a positive factor
+        v = A @ Z[:, k]
+        cos = v @ U[:, k] / np.linalg.norm(v)
+        assert abs(cos - 1.0) < 1e-13
+
+
+def test_cccp_theorem1_invariants():
+    n, n_r = 24, 10
+    U, _ = _ubar(n, n_r, 2)
+    gamma, rho, eps = 0.1, 0.05, 1e-8
+    S = np.eye(n)
+    for _ in range(15):
+        F = O.cccp_map_F(S, U, gamma, eps)
+        St = (1 - rho) * F + rho * np.eye(n)
+        assert np.linalg.eigvalsh(St)[0] >= rho * (1 - 1e-12)   # Sigma~ >= rho I
+        S_next = O.cccp_fit(U, gamma, rho, eps, max_iter=1, Sigma0=S).Sigma
+        np.testing.assert_allclose(S_next, St / (np.trace(St) / n), rtol=1e-12, atol=1e-14)
+        assert abs(np.trace(S_next) - n) < 1e-10 * n             # tr = n
+        assert np.abs(S_next - S_next.T).max() < 1e-12           # symmetric
+        assert np.linalg.eigvalsh(S_next)[0] > 0
+        S = S_next
+    res = O.cccp_fit(U, gamma, rho, eps, max_iter=500, tol=1e-12)
+    assert res.converged
+    # fixed point of T (Theorem 1)
+    again = O.cccp_fit(U, gamma, rho, eps, max_iter=1, Sigma0=res.Sigma).Sigma
+    assert np.linalg.norm(again - res.Sigma) / np.linalg.norm(res.Sigma) < 1e-10
+
+
+def _sym_dirs(S, k, seed):
+    """Random symmetric directions scaled to S (S^1/2 H S^1/2), so a finite
+    step is small relative to every eigenvalue of S."""
+    n = S.shape[0]
+    w, V = np.linalg.eigh(S)
+    Sh = (V * np.sqrt(w)) @ V.T
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(k):
+        H = rng.normal(size=(n, n))
+        out.append(Sh @ ((H + H.T) / 2) @ Sh)
+    return out
+
+
+def test_cccp_gamma0_reaches_tyler_fixed_point_and_is_stationary():
+    """gamma = rho = eps = 0: the normalised iteration is Tyler's estimator;
+    its limit satisfies Eq. tyler-fixed-point with tr = n and is a stationary
+    point of the scale-invariant ACG likelihood (Sec. IV-A)."""
+    n, n_r = 8, 40
+    U, _ = _ubar(n, n_r, 3)
+    res = O.cccp_fit(U, 0.0, 0.0, 0.0, max_iter=5000, tol=1e-14)
+    S = res.Sigma
+    Sinv = np.linalg.inv(S)
+    rhs = np.zeros((n, n))
+    for k in range(n_r):
+        u = U[:, k]
+        rhs += np.outer(u, u) / (u @ Sinv @ u)
+    rhs *= n / n_r
+    np.testing.assert_allclose(S, rhs, rtol=1e-9, atol=1e-11)
+    assert abs(np.trace(S) - n) < 1e-9
+    f0 = O.mle_objective(S, U, 0.0)
+    h = 1e-5
+    for H in _sym_dirs(S, 4, 8):
+        g = (O.mle_objective(S + h * H, U, 0.0) - O.mle_objective(S - h * H, U, 0.0)) / (2 * h)
+        assert abs(g) < 1e-6 * max(1.0, abs(f0))
+
+
+def test_unnormalised_cccp_is_monotone_and_stationary():
+    """gamma > 0, rho = eps = 0, no normalisation: CCCP (Sec. IV-C) is a
+    majorise-minimise scheme for Eq. prob:kernel-mle; the objective never
+    increases and the limit has zero directional derivatives."""
+    n, n_r = 8, 40
+    U, _ = _ubar(n, n_r, 4)
+    gamma = 0.3
+    S = np.eye(n)
+    prev = O.mle_objective(S, U, gamma)
+    for _ in range(60):
+        S = O.cccp_fit(U, gamma, 0.0, 0.0, max_iter=1, normalize=False, Sigma0=S).Sigma
+        cur = O.mle_objective(S, U, gamma)
+        assert cur <= prev + 1e-12 * abs(prev)
+        prev = cur
+    res = O.cccp_fit(U, gamma, 0.0, 0.0, max_iter=20000, tol=1e-14, normalize=False)
+    S = res.Sigma
+    f0 = O.mle_objective(S, U, gamma)
+    h = 1e-5
+    for H in _sym_dirs(S, 4, 9):
+        g = (O.mle_objective(S + h * H, U, gamma) - O.mle_objective(S - h * H, U, gamma)) / (2 * h)
+        assert abs(g) < 1e-6 * max(1.0, abs(f0))
+
+
+def test_inverse_sqrt_property():
+    U, _ = _ubar(30, 12, 5)
+    S = O.cccp_fit(U, 0.1, 0.1, 1e-8, max_iter=50).Sigma
+    P = O.inverse_sqrt(S)
+    np.testing.assert_allclose(P @ S @ P, np.eye(30), atol=1e-10)
+    np.testing.assert_allclose(P, P.T, atol=1e-14)
+    assert np.linalg.eigvalsh(P)[0] > 0
+
+
+def test_cccp_preconditioner_reduces_condition_number():
+    """Sec. V-B: the learned P shrinks kappa by orders of magnitude while
+    Jacobi barely changes it; PCG iterations order accordingly."""
+    n = 512
+    inst = synth.make_instance(n, 16, 1e-3, seed=21, grid=2)
+    Z = synth.directions(n, synth.default_num_directions(n), 21)
+    r = O.laker(inst.Q, inst.y, inst.lam, inst.scale, Z, tol=1e-8)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    kA = O.condition_number(A)
+    kPA = O.condition_number(A, r.P)
+    kJ = O.condition_number(A, O.jacobi_preconditioner(A))
+    assert kPA < kA / 10
+    assert kJ > kA / 3
+    it_j = O.pcg(A, inst.y, O.jacobi_preconditioner(A), 1e-8).iterations
+    assert r.pcg.iterations < it_j
+
+
+# --------------------------------------------------------------------------
+# Metrics and the radio map
+# --------------------------------------------------------------------------
+
+def test_direct_solution_minimises_R():
+    """Sec. III / V-A: the minimiser of R(alpha) solves (G + lambda I) alpha = y
+    (G is invertible here); finite differences of R vanish at alpha*."""
+    inst = synth.make_instance(40, 6, 1e-1, seed=13, grid=2)
+    G = O.kernel_matrix(inst.Q, inst.scale)
+    A = G + inst.lam * np.eye(40)
+    a = O.solve_direct(A, inst.y)
+    rng = np.random.default_rng(1)
+    h = 1e-4
+    base = O.objective_R(G, a, inst.y, inst.lam)
+    for _ in range(5):
+        v = rng.normal(size=40)
+        g = (O.objective_R(G, a + h * v, inst.y, inst.lam)
+             - O.objective_R(G, a - h * v, inst.y, inst.lam)) / (2 * h)
+        assert abs(g) < 1e-6 * max(1.0, base)
+    assert O.objective_gap(G, a, a, inst.y, inst.lam) == 0.0
+    assert O.prediction_discrepancy(G, a, a) == 0.0
+    assert O.relative_residual(A, a, inst.y) < 1e-12
+
+
+def test_radio_map_at_training_points_is_y_minus_lambda_alpha():
+    """From (G + lambda I) alpha = y: r(x_i) = (G alpha)_i = y_i - lambda alpha_i."""
+    inst = synth.make_instance(50, 8, 1e-2, seed=17, grid=2)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    a = O.solve_direct(A, inst.y)
+    f = O.radio_map(inst.Q, inst.Q, a, inst.scale)
+    np.testing.assert_allclose(f, inst.y - inst.lam * a, rtol=1e-9, atol=1e-9)
+
+
+def test_rmse_nmse_closed_forms():
+    t = np.array([1.0, -2.0, 3.0, 0.5])
+    p = t + np.array([0.1, -0.1, 0.2, 0.0])
+    assert abs(O.rmse(p, t) - math.sqrt((0.01 + 0.01 + 0.04) / 4)) < 1e-15
+    assert abs(O.nmse(p, t) - 0.06 / (1 + 4 + 9 + 0.25)) < 1e-15
+
+
+def test_cccp_map_at_identity_closed_form_trace():
+    """At Sigma = I every quadratic form u_k^T u_k is 1, so
+    tr F_gamma(I) = n (1/(1 + eps) + gamma) / (1 + gamma/n) in closed form
+    (Eq. kernel_shrinkage_cccp_F)."""
+    n, n_r = 15, 9
+    U, _ = _ubar(n, n_r, 6)
+    for gamma, eps in ((0.3, 0.5), (0.0, 2.0), (1.7, 0.0)):
+        F = O.cccp_map_F(np.eye(n), U, gamma, eps)
+        want = n * (1.0 / (1.0 + eps) + gamma) / (1.0 + gamma / n)
+        assert abs(np.trace(F) - want) < 1e-12 * want
+        # and F - gamma I/(1+gamma/n) has rank <= N_r
+        R = F - gamma / (1 + gamma / n) * np.eye(n)
+        assert np.linalg.matrix_rank(R, tol=1e-10) <= n_r
+
+
+def test_shrinkage_rule_reading():
+    assert O.shrinkage_rho(100, 100, 0.1) == 1e-3
+    assert O.shrinkage_rho(100, 200, 0.1) == 1e-3
+    vals = [O.shrinkage_rho(1000, m, 0.1) for m in (900, 500, 100, 10)]
+    assert all(a <= b for a, b in zip(vals, vals[1:]))
+    assert O.shrinkage_rho(1000, 10, 5.0) == 0.5
