@@ -1,0 +1,357 @@
+"""Benchmark: PCG solves/s at a true relative residual of 1e-6 on one large
+radio-map instance (n = 16384 clustered locations, d = 32, lambda = 1e-4,
+8 transmitters, 512 x 512 query grid).
+
+One step = the whole hot path on one instance: kernel construction, CCCP
+preconditioner fit (N_r random directions), mixed-precision PCG with a
+float64-accurate residual every 20 products, radio-map evaluation.  Inputs are
+resident in HBM when the timed region starts (`value`); `e2e` repeats the
+step through the same public API with pinned host buffers copied in and the
+results copied out inside the timed region.  The plain float64 path (the
+paper's method run in float64 throughout) is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the instance does not shard; N ranks run N independent replicas
+(different seeds), `value` = instances solved by all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_25138_gb300 import synth  # noqa: E402
+
+METRIC = "PCG solves/s at rel-res 1e-6 (mixed)"
+UNIT = "solves/s"
+CFG = dict(n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6, refine_every=20)
+SEED = 2000
+
+
+def workload(seed: int):
+    c = CFG
+    inst = synth.make_instance(c["n"], c["d"], c["lam"], n_tx=c["n_tx"], seed=seed, layout=c["layout"],
+                               grid=c["grid"])
+    n_r = synth.default_num_directions(c["n"])
+    Z = synth.directions(c["n"], n_r, seed)
+    return inst, Z, n_r
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, device: int):
+        self.proc = None
+        self.device = device
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+        return False
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Our CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_25138_gb300 import build
+    from paper_2604_25138_gb300 import laker as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    dev_t = torch.device("cuda", local)
+    inst, Zh, n_r = workload(SEED + rank)
+    c = CFG
+
+    def to_dev(x):
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev_t)
+
+    Q, y, Z, Qg = to_dev(inst.Q), to_dev(inst.y), to_dev(Zh), to_dev(inst.Qg)
+    ctx = L.Context(local)
+
+    def step(Q, y, Z, Qg, precision, refine):
+        op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, precision)
+        P = L.laker_fit_preconditioner(ctx, op, Z)
+        alpha, info = L.laker_pcg_solve(ctx, op, P, y, c["tol"], max_iter=20000, refine_every=refine)
+        fmap = L.laker_eval_map(ctx, op, Qg, alpha)
+        P.close()
+        op.close()
+        return alpha, fmap, info, P.info
+
+    mixed = dict(precision=L.FP32, refine=c["refine_every"])
+    for _ in range(args.warmup):
+        step(Q, y, Z, Qg, **mixed)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(ctx.stream)
+        t0 = time.perf_counter()
+        infos = []
+        for _ in range(args.steps):
+            alpha, fmap, info, finfo = step(Q, y, Z, Qg, **mixed)
+            infos.append((info, finfo))
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = ctx.launches() - launches0
+    dev_ms = ev0.elapsed_time(ev1)
+    ms = max(dev_ms, wall * 1e3)
+    if world > 1:
+        t = torch.tensor([ms], device=dev_t)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    info, finfo = infos[-1]
+
+    # end to end through the public API with pinned host buffers
+    hosts = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (inst.Q, inst.y, Zh, inst.Qg)]
+    h2d = sum(h.numel() * 8 for h in hosts)
+    out_a = torch.empty(inst.n, dtype=torch.float64).pin_memory()
+    out_m = torch.empty(inst.Qg.shape[0], dtype=torch.float64).pin_memory()
+    d2h = (out_a.numel() + out_m.numel()) * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        dQ, dy, dZ, dQg = (h.to(dev_t, non_blocking=True) for h in hosts)
+        a, fm, _, _ = step(dQ, dy, dZ, dQg, **mixed)
+        out_a.copy_(a, non_blocking=True)
+        out_m.copy_(fm, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    # roofline of the dominant kernel: the streamed float32 matvec of G
+    op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32)
+    x = to_dev(synth.random_vector(inst.n, 1))
+    w = torch.empty_like(x)
+    for _ in range(3):
+        L.laker_op_matvec(ctx, op, x, w)
+    reps = 30
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        L.laker_op_matvec(ctx, op, x, w)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1) / reps
+    n = inst.n
+    ldk = (n + 3) // 4 * 4
+    mv_bytes = n * ldk * 4 + 3 * n * 8
+    peak, peak_kind = peaks()
+    achieved = mv_bytes / (mv_ms * 1e-3) / 1e9
+    op.close()
+
+    # plain float64 path on the same instance (the paper's method in float64)
+    plain = None
+    if args.plain_steps > 0:
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        for _ in range(args.plain_steps):
+            _, _, pinfo, _ = step(Q, y, Z, Qg, precision=L.FP64, refine=0)
+        torch.cuda.synchronize()
+        pm = (time.perf_counter() - p0) * 1e3 / args.plain_steps
+        plain = {"solves_per_s": 1e3 / pm, "ms_per_step": pm, "iterations": pinfo["iterations"],
+                 "rel_res_true": pinfo["rel_res_true"]}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(inst, Zh, n_r, info["iterations"] if plain is None else plain["iterations"],
+                              finfo["iterations"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "single instance, n=16384 clustered, d=32, lambda=1e-4, 8 Tx, 512x512 grid, "
+                               "N_r=%d, tol 1e-6 true residual" % n_r,
+                   "n": n, "d": inst.d, "lambda": inst.lam, "n_r": n_r, "grid": CFG["grid"] ** 2,
+                   "operator": "materialised float32 G, float64 residual every 20 products",
+                   "l2": "inputs larger than L2 (G is 1 GiB float32 + 2 GiB float64)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "solve": {"iterations": info["iterations"], "true_residuals": info["true_residuals"],
+                  "rel_res_true": info["rel_res_true"], "cccp_iterations": finfo["iterations"]},
+        "plain_fp64": plain,
+        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "k_matvec_mat<float> (streamed G, fused PCG epilogue)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "bytes_per_launch": mv_bytes,
+                     "ms_per_launch": mv_ms},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+
+def oracle_baseline(inst, Z, n_r, pcg_iterations, cccp_iterations, budget_s: float = 25.0):
+    """Time the oracle's steps on a bounded sample and scale to one solve:
+    kernel build at full n; 5 PCG iterations at full n (dense matvec and dense
+    P apply) scaled by the iteration count; one dense CCCP iteration and the
+    dense Sigma^-1/2 at n_s = 2048 scaled by (n/n_s)^3 and the CCCP iteration
+    count; the map on 1/64 of the grid scaled by 64."""
+    from oracle import laker_oracle as O
+    n = inst.n
+    t0 = time.perf_counter()
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    t_build = time.perf_counter() - t0
+    P = O.jacobi_preconditioner(A)       # a dense n x n stand-in with the cost of a dense P apply
+    t0 = time.perf_counter()
+    O.pcg(A, inst.y, P, 0.0, max_iter=5)
+    t_iter = (time.perf_counter() - t0) / 5
+    del P
+    ns = 2048
+    Us = O.random_directions(A[:ns, :ns], Z[:ns, :min(n_r, ns)])
+    t0 = time.perf_counter()
+    cc = O.cccp_fit(Us, 0.1, 0.1, 1e-8, max_iter=1)
+    t_cccp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.inverse_sqrt(cc.Sigma)
+    t_eig = time.perf_counter() - t0
+    scale3 = (n / ns) ** 3
+    t_fit = (t_cccp * cccp_iterations + t_eig) * scale3
+    m = inst.Qg.shape[0]
+    ms_ = m // 64
+    t0 = time.perf_counter()
+    O.radio_map(inst.Qg[:ms_], inst.Q, np.zeros(n), inst.scale)
+    t_map = (time.perf_counter() - t0) * 64
+    total = t_build + t_fit + pcg_iterations * t_iter + t_map
+    return {"value": 1.0 / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": ("numpy float64 oracle: build at full n (%.2fs); 5 PCG iterations at full n (%.3fs each) x %d "
+                       "iterations; one dense CCCP iteration (%.2fs) and Sigma^-1/2 (%.2fs) at n=2048 scaled by "
+                       "(n/2048)^3 and %d CCCP iterations; map on 1/64 of the grid x 64 (%.2fs); estimated "
+                       "%.1fs per solve" % (t_build, t_iter, pcg_iterations, t_cccp, t_eig, cccp_iterations,
+                                            t_map, total))}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst, Zh, n_r = workload(SEED)
+    # iteration counts of the float64 method on this instance (measured on the
+    # GPU path; the oracle's own PCG needs the same order of iterations)
+    its, cccp_its = args.ref_iterations, args.ref_cccp_iterations
+    vals = []
+    for _ in range(args.warmup):
+        oracle_baseline(inst, Zh, n_r, its, cccp_its)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_baseline(inst, Zh, n_r, its, cccp_its))
+    wall = time.perf_counter() - t0
+    v = statistics.median([b["value"] for b in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single instance, n=16384 clustered, d=32, lambda=1e-4, 8 Tx, 512x512 grid"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": vals[-1]["sample"] + "; wall %.1fs for %d samples" % (wall, args.steps)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iterations", type=int, default=1500)
+    ap.add_argument("--ref-cccp-iterations", type=int, default=30)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

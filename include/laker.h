@@ -1,0 +1,177 @@
+/*
+ * laker.h -- C ABI of the GB300 (sm_103a) implementation of the LAKER hot path:
+ * regularized attention-kernel regression solved by preconditioned conjugate
+ * gradients with a CCCP-learned preconditioner (arXiv 2604.25138).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Array arguments are DEVICE pointers owned by the caller, unless the name
+ *   ends in `_host`.  Matrices are row-major and contiguous.  Floating-point
+ *   inputs and outputs are float64 whatever precision the library computes in.
+ * - Work is issued on the stream given to laker_create(); calls that return
+ *   an info struct synchronise that stream before returning, the others are
+ *   asynchronous.
+ * - Handles (laker_ctx, laker_op, laker_precond) are owned by the library from
+ *   their create/build call until the matching destroy call.  All device
+ *   workspace is allocated at create/build/fit time and freed by destroy; the
+ *   solve, apply and map calls allocate nothing unless noted.
+ * - Every call returns a laker_status (0 = success, < 0 = error).  No call
+ *   aborts, traps or prints.  laker_last_error() gives a message for the last
+ *   failing call on a context.  Errors in device code are reported through a
+ *   status word and never by a trap.
+ */
+#ifndef LAKER_H
+#define LAKER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LAKER_OK = 0,
+    LAKER_ERR_ARG = -1,          /* invalid argument (sizes, NULL, lambda <= 0) */
+    LAKER_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    LAKER_ERR_NOT_SPD = -3,      /* a Cholesky factorisation met a non-positive pivot */
+    LAKER_ERR_BREAKDOWN = -4,    /* PCG breakdown: p^T A p <= 0 or r^T z <= 0 or non-finite */
+    LAKER_ERR_MAXITER = -5,      /* tolerance not reached; the best alpha is still written */
+    LAKER_ERR_NONFINITE = -6,    /* NaN or Inf found in an input */
+    LAKER_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up */
+    LAKER_ERR_OOM = -8,          /* device allocation failed */
+    LAKER_ERR_UNSUPPORTED = -9   /* combination of options not built */
+} laker_status;
+
+/* Arithmetic of the kernel operator (Sec. III-A, Eq. sc-exp-kernel). */
+typedef enum {
+    LAKER_FP64 = 0,      /* float64 logits, exp and accumulation */
+    LAKER_FP32 = 1,      /* float32 storage / arithmetic, float64 PCG scalars */
+    LAKER_BF16X3 = 2     /* split-bf16 logits on tensor cores, float32 exp and sums */
+} laker_precision;
+
+/* How the operator v -> (lambda I + G) v is evaluated. */
+typedef enum {
+    LAKER_AUTO = 0,
+    LAKER_MATERIALISED = 1,   /* G stored in HBM, streamed each product */
+    LAKER_MATRIX_FREE = 2     /* G recomputed tile by tile from Q each product */
+} laker_variant;
+
+typedef struct laker_ctx laker_ctx;
+typedef struct laker_op laker_op;
+typedef struct laker_precond laker_precond;
+
+typedef struct {
+    int iterations;      /* CCCP updates applied */
+    int converged;       /* 1 if the relative Frobenius change fell below tol */
+    double c;            /* Sigma_* = c I + U diag(D) U^T, isotropic part */
+    double rho;          /* shrinkage used */
+    double change;       /* last relative Frobenius change |S_{t+1}-S_t|_F/|S_t|_F */
+    int status;          /* laker_status of the fit */
+} laker_fit_info;
+
+typedef struct {
+    int iterations;      /* number of operator products (lambda I + G) p */
+    int true_residuals;  /* number of float64-accurate residual recomputations */
+    int converged;       /* 1 if the stopping test held */
+    double rel_res;      /* |r|/|y| of the recursive residual at exit */
+    double rel_res_true; /* |y - (lambda I + G) alpha| / |y| (float64 operator) */
+    int status;          /* laker_status of the solve */
+} laker_solve_info;
+
+/* Context: binds a device and a CUDA stream (cudaStream_t passed as void*).
+ * The stream must not be the legacy default stream, because solves capture
+ * their iterations into CUDA graphs; NULL makes the library create and own a
+ * non-blocking stream, which callers then order against their own work. */
+laker_status laker_create(laker_ctx** ctx, int device, void* stream);
+laker_status laker_destroy(laker_ctx* ctx);
+const char* laker_last_error(const laker_ctx* ctx);
+const char* laker_status_string(int status);
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t laker_launch_count(const laker_ctx* ctx);
+
+/*
+ * Kernel construction (Algorithm 1, kernel-construction stage; Sec. III-A,
+ * Eqs. sc-exp-kernel and sc-final):  G_ij = exp(scale * <q_i, q_j>), operator
+ * v -> lambda v + G v.
+ *   Q       n x d embeddings (device, float64, row-major); copied, the caller
+ *           may free it after the call returns.
+ *   scale   1.0 reproduces the paper's exp(<e_i,e_j>); 1/sqrt(d) gives the
+ *           scaled dot-product form.
+ *   lambda  ridge parameter, must be > 0.
+ *   precision / variant  see the enums.  FP32 and BF16X3 operators also keep a
+ *           float64-accurate materialised G for true-residual recomputation.
+ * Errors: LAKER_ERR_ARG for n < 1, d < 1 or d > 256, lambda <= 0;
+ *         LAKER_ERR_OOM if G does not fit.
+ */
+laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int d,
+                                double scale, double lambda, int precision, int variant,
+                                laker_op** op);
+laker_status laker_op_destroy(laker_op* op);
+
+/* w = (lambda I + G) x with the operator's inner precision (device n-vectors). */
+laker_status laker_op_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
+/* w = (lambda I + G) x with the float64-accurate operator. */
+laker_status laker_op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
+
+/*
+ * Preconditioner learning (Algorithm 1, learning stage; Sec. IV-B Eq.
+ * random_directions, Sec. IV-D Eqs. kernel_shrinkage_cccp_F/_Sigma/
+ * _normalization, Eq. preconditioner-Sigmma):
+ *   u_k = (lambda I + G) z_k, u_k <- u_k/|u_k|;  Sigma_0 = I;
+ *   Sigma_{t+1} = normalise((1-rho) F_gamma(Sigma_t) + rho I)  until the
+ *   relative Frobenius change is <= tol or max_iter updates;
+ *   P = Sigma_*^(-1/2).
+ * The iterate is kept exactly as Sigma_t = c I + U diag(D) U^T (N_r directions).
+ *   Z       n x n_r Gaussian directions (device, float64, column k = z_k).
+ *   rho     < 0 selects the adaptive rule min(1/2, max(1e-3, gamma (1 - n_r/n)))
+ *           (1e-3 when n_r >= n).
+ *   eps     safeguard of F_gamma (> 0).
+ * Errors: LAKER_ERR_ARG for n_r < 1 or n_r > 1024; LAKER_ERR_NOT_SPD if a
+ * factorisation fails.
+ */
+laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z,
+                                      int n_r, double gamma, double rho, double eps,
+                                      int max_iter, double tol, laker_precond** P,
+                                      laker_fit_info* info);
+/* Jacobi preconditioner P_J = diag(lambda I + G)^-1 (Sec. V-A baselines). */
+laker_status laker_precond_jacobi(laker_ctx* ctx, const laker_op* op, laker_precond** P);
+laker_status laker_precond_destroy(laker_precond* P);
+/* z = P r (device n-vectors). */
+laker_status laker_precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
+/* Export the CCCP state: c (1 value), D (n_r values), Ubar (n x n_r), all
+ * device float64; any pointer may be NULL. */
+laker_status laker_precond_export(laker_ctx* ctx, const laker_precond* P, double* c, double* D,
+                                  double* Ubar);
+
+/*
+ * PCG solve of (lambda I + G) alpha = y (Sec. IV-E, Algorithm 1, PCG stage):
+ *   alpha^0 = 0, r^0 = y, z^0 = P r^0, p^0 = z^0; delta = r.z / p.Ap;
+ *   alpha += delta p; r -= delta Ap; stop if |r|/|y| <= tol; z = P r;
+ *   beta = r.z_new / r.z_old; p = z + beta p.
+ *   P          NULL = identity.
+ *   tol        relative residual tolerance.
+ *   refine_every  k > 0 (FP32 / BF16X3 operators): every k products, and
+ *              whenever the recursive residual passes the test, r is replaced
+ *              by y - (lambda I + G) alpha computed with the float64-accurate
+ *              operator, and the stop test uses that true residual.  0 = never.
+ * alpha (device, n) receives the last iterate, also on LAKER_ERR_MAXITER.
+ */
+laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
+                             const double* y, double* alpha, double tol, int max_iter,
+                             int refine_every, laker_solve_info* info);
+
+/*
+ * Radio-map reconstruction (Sec. III-A, Eq. sc-radio-map-reconstruction;
+ * Algorithm 1, reconstruction stage):  out_m = sum_i exp(scale <qg_m, q_i>) alpha_i.
+ *   Qg   m x d query embeddings (device float64);  alpha, out device float64.
+ * Computed in the operator's precision (FP64, or split-bf16 logits with
+ * float32 exp and float64 partial sums).
+ */
+laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                            const double* alpha, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAKER_H */

@@ -1,0 +1,283 @@
+// C ABI of liblaker: argument checks, handle lifetime, dispatch.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "laker_internal.h"
+
+laker_status pcg_prepare(laker_ctx* ctx);
+
+laker_status set_error(laker_ctx* ctx, laker_status st, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+laker_status lk_malloc(laker_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(ctx, LAKER_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                                 "): " + cudaGetErrorString(e));
+    }
+    return LAKER_OK;
+}
+
+namespace {
+
+laker_status check_ctx(laker_ctx* ctx) {
+    if (!ctx) return LAKER_ERR_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e));
+    return LAKER_OK;
+}
+
+void free_op(laker_op* op) {
+    if (!op) return;
+    cudaFree(op->Q64);
+    cudaFree(op->Qhi);
+    cudaFree(op->Qlo);
+    cudaFree(op->Q32);
+    cudaFree(op->K64);
+    cudaFree(op->K32);
+    cudaFree(op->diagA);
+    delete op;
+}
+
+void free_precond(laker_precond* P) {
+    if (!P) return;
+    cudaFree(P->D);
+    cudaFree(P->U64);
+    cudaFree(P->W64);
+    cudaFree(P->U32);
+    cudaFree(P->W32);
+    cudaFree(P->dinv);
+    delete P;
+}
+
+__global__ void k_recip(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = 1.0 / x[i];
+}
+
+__global__ void k_nonfinite(int64_t count, const double* __restrict__ x, int* flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count && !isfinite(x[i])) atomicExch(flag, 1);
+}
+
+// Returns LAKER_ERR_NONFINITE if any of x[0..count) is NaN/Inf.
+laker_status scan_finite(laker_ctx* ctx, const double* x, int64_t count) {
+    int* flag = nullptr;
+    laker_status st = lk_malloc(ctx, (void**)&flag, sizeof(int));
+    if (st != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    k_nonfinite<<<(unsigned)((count + 255) / 256), 256, 0, ctx->stream>>>(count, x, flag);
+    LK_LAUNCHED(ctx);
+    int h = 0;
+    LK_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(flag);
+    return h ? set_error(ctx, LAKER_ERR_NONFINITE, "non-finite value in input") : LAKER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+laker_status laker_create(laker_ctx** out, int device, void* stream) {
+    if (!out) return LAKER_ERR_ARG;
+    *out = nullptr;
+    laker_ctx* ctx = new (std::nothrow) laker_ctx();
+    if (!ctx) return LAKER_ERR_OOM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete ctx; return LAKER_ERR_CUDA; }
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete ctx; return LAKER_ERR_CUDA; }
+        ctx->owns_stream = true;
+    }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->num_sms <= 0) ctx->num_sms = 1;
+    laker_status st = pcg_prepare(ctx);
+    if (st != LAKER_OK) { laker_destroy(ctx); return st; }
+    *out = ctx;
+    return LAKER_OK;
+}
+
+laker_status laker_destroy(laker_ctx* ctx) {
+    if (!ctx) return LAKER_ERR_ARG;
+    if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LAKER_OK;
+}
+
+const char* laker_last_error(const laker_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+const char* laker_status_string(int status) {
+    switch (status) {
+        case LAKER_OK: return "ok";
+        case LAKER_ERR_ARG: return "invalid argument";
+        case LAKER_ERR_CUDA: return "CUDA error";
+        case LAKER_ERR_NOT_SPD: return "matrix not positive definite";
+        case LAKER_ERR_BREAKDOWN: return "PCG breakdown";
+        case LAKER_ERR_MAXITER: return "maximum iterations reached";
+        case LAKER_ERR_NONFINITE: return "non-finite input";
+        case LAKER_ERR_TIMEOUT: return "device wait timed out";
+        case LAKER_ERR_OOM: return "out of device memory";
+        case LAKER_ERR_UNSUPPORTED: return "unsupported option combination";
+        default: return "unknown status";
+    }
+}
+
+int64_t laker_launch_count(const laker_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int d, double scale, double lambda,
+                                int precision, int variant, laker_op** out) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!out || !Q) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (n < 1 || d < 1 || d > 256) return set_error(ctx, LAKER_ERR_ARG, "need n >= 1 and 1 <= d <= 256");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return set_error(ctx, LAKER_ERR_ARG, "need lambda > 0");
+    if (!std::isfinite(scale)) return set_error(ctx, LAKER_ERR_ARG, "scale not finite");
+    if (precision < LAKER_FP64 || precision > LAKER_BF16X3) return set_error(ctx, LAKER_ERR_ARG, "bad precision");
+    if (variant < LAKER_AUTO || variant > LAKER_MATRIX_FREE) return set_error(ctx, LAKER_ERR_ARG, "bad variant");
+    if (variant == LAKER_AUTO)
+        variant = (precision == LAKER_BF16X3) ? LAKER_MATRIX_FREE : LAKER_MATERIALISED;
+    if (precision == LAKER_BF16X3) variant = LAKER_MATRIX_FREE;
+    if (precision != LAKER_BF16X3 && variant == LAKER_MATRIX_FREE)
+        return set_error(ctx, LAKER_ERR_UNSUPPORTED, "the matrix-free operator uses split-bf16 logits (BF16X3)");
+    if ((st = scan_finite(ctx, Q, n * d)) != LAKER_OK) return st;
+    laker_op* op = new (std::nothrow) laker_op();
+    if (!op) return LAKER_ERR_OOM;
+    op->ctx = ctx;
+    op->n = n;
+    op->d = d;
+    op->scale = scale;
+    op->lambda = lambda;
+    op->precision = precision;
+    op->variant = variant;
+    if ((st = lk_malloc(ctx, (void**)&op->Q64, (size_t)n * d * sizeof(double))) != LAKER_OK) { free_op(op); return st; }
+    cudaError_t e = cudaMemcpyAsync(op->Q64, Q, (size_t)n * d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) { free_op(op); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    if ((st = build_operator(ctx, op)) != LAKER_OK) { free_op(op); return st; }
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { free_op(op); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    *out = op;
+    return LAKER_OK;
+}
+
+laker_status laker_op_destroy(laker_op* op) {
+    if (!op) return LAKER_ERR_ARG;
+    cudaSetDevice(op->ctx->device);
+    free_op(op);
+    return LAKER_OK;
+}
+
+laker_status laker_op_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !x || !w) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    return op_matvec_inner(ctx, op, x, w);
+}
+
+laker_status laker_op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !x || !w) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    return op_matvec_fp64(ctx, op, x, w);
+}
+
+laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma,
+                                      double rho, double eps, int max_iter, double tol, laker_precond** out,
+                                      laker_fit_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !Z || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (n_r < 1 || n_r > 1024) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 1024");
+    if (!(gamma >= 0.0) || !(eps > 0.0) || rho > 1.0 || max_iter < 1 || !(tol >= 0.0))
+        return set_error(ctx, LAKER_ERR_ARG, "bad CCCP parameters");
+    if ((st = scan_finite(ctx, Z, op->n * (int64_t)n_r)) != LAKER_OK) return st;
+    laker_precond* P = new (std::nothrow) laker_precond();
+    if (!P) return LAKER_ERR_OOM;
+    P->ctx = ctx;
+    P->use32 = op->precision != LAKER_FP64;
+    st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info);
+    if (st != LAKER_OK) { free_precond(P); return st; }
+    *out = P;
+    return LAKER_OK;
+}
+
+laker_status laker_precond_jacobi(laker_ctx* ctx, const laker_op* op, laker_precond** out) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    laker_precond* P = new (std::nothrow) laker_precond();
+    if (!P) return LAKER_ERR_OOM;
+    P->ctx = ctx;
+    P->kind = PRECOND_JACOBI;
+    P->n = op->n;
+    if ((st = lk_malloc(ctx, (void**)&P->dinv, (size_t)op->n * sizeof(double))) != LAKER_OK) { free_precond(P); return st; }
+    k_recip<<<(unsigned)((op->n + 255) / 256), 256, 0, ctx->stream>>>(op->n, op->diagA, P->dinv);
+    ctx->launches++;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { free_precond(P); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    *out = P;
+    return LAKER_OK;
+}
+
+laker_status laker_precond_destroy(laker_precond* P) {
+    if (!P) return LAKER_ERR_ARG;
+    cudaSetDevice(P->ctx->device);
+    free_precond(P);
+    return LAKER_OK;
+}
+
+laker_status laker_precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!P || !r || !z) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    return precond_apply(ctx, P, r, z);
+}
+
+laker_status laker_precond_export(laker_ctx* ctx, const laker_precond* P, double* c, double* D, double* Ubar) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!P) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (P->kind != PRECOND_CCCP) return set_error(ctx, LAKER_ERR_ARG, "not a CCCP preconditioner");
+    if (c) LK_CUDA(ctx, cudaMemcpyAsync(c, &P->c, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (D) LK_CUDA(ctx, cudaMemcpyAsync(D, P->D, P->n_r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (Ubar)
+        LK_CUDA(ctx, cudaMemcpyAsync(Ubar, P->U64, (size_t)P->n * P->n_r * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LAKER_OK;
+}
+
+laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
+                             double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !y || !alpha) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (!(tol >= 0.0) || max_iter < 1 || refine_every < 0) return set_error(ctx, LAKER_ERR_ARG, "bad PCG parameters");
+    if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
+    if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
+    return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info);
+}
+
+laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
+                            double* out) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !Qg || !alpha || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (m < 1) return set_error(ctx, LAKER_ERR_ARG, "need m >= 1");
+    return eval_map(ctx, op, Qg, m, alpha, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Kernel construction: G_ij = exp(scale <q_i, q_j>)  (Sec. III-A,
+// Eq. sc-exp-kernel; Algorithm 1, kernel-construction stage).
+//
+// G is symmetric, so only tiles (bi <= bj) are evaluated and each off-diagonal
+// tile is written twice (direct and, through a shared-memory transpose,
+// mirrored), halving the float64 exponentials -- the dominant cost on GB300,
+// whose float64 pipe runs at ~1/74 of the float32 rate.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "laker_device.cuh"
+
+namespace {
+
+constexpr int BT = 64;   // output tile edge
+constexpr int BD = 32;   // embedding-dimension chunk
+
+template <bool W32>
+__global__ void __launch_bounds__(256)
+k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
+            double* __restrict__ K64, float* __restrict__ K32, int64_t ldk, int nt) {
+    // blockIdx.x enumerates the upper-triangular tile pairs row by row.
+    int64_t t = blockIdx.x;
+    int bi = 0;
+    while (t >= nt - bi) { t -= nt - bi; ++bi; }
+    const int bj = bi + (int)t;
+
+    __shared__ double sm[2 * BD * (BT + 1)];
+    double (*Qi)[BT + 1] = reinterpret_cast<double (*)[BT + 1]>(sm);
+    double (*Qj)[BT + 1] = reinterpret_cast<double (*)[BT + 1]>(sm + BD * (BT + 1));
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+
+    for (int k0 = 0; k0 < d; k0 += BD) {
+        for (int idx = threadIdx.x; idx < BT * BD; idx += blockDim.x) {
+            const int r = idx / BD, k = idx % BD;
+            const int64_t gi = (int64_t)bi * BT + r, gj = (int64_t)bj * BT + r;
+            const bool kin = (k0 + k) < d;
+            Qi[k][r] = (gi < n && kin) ? Q[gi * d + k0 + k] : 0.0;
+            Qj[k][r] = (gj < n && kin) ? Q[gj * d + k0 + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < BD; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = Qi[k][ty + 16 * u]; b[u] = Qj[k][tx + 16 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+
+    // exp, direct store, stage for the mirrored store
+    double (*T)[BT + 1] = reinterpret_cast<double (*)[BT + 1]>(sm);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = ty + 16 * u;
+        const int64_t i = (int64_t)bi * BT + r;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int c = tx + 16 * v;
+            const int64_t j = (int64_t)bj * BT + c;
+            const double g = exp(scale * acc[u][v]);
+            T[r][c] = g;
+            if (i < n && j < n) {
+                K64[i * ldk + j] = g;
+                if (W32) K32[i * ldk + j] = (float)g;
+            }
+        }
+    }
+    if (bi == bj) return;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < BT * BT; idx += blockDim.x) {
+        const int c = idx / BT, r = idx % BT;   // output row bj*BT + c, column bi*BT + r
+        const int64_t oi = (int64_t)bj * BT + c, oj = (int64_t)bi * BT + r;
+        if (oi < n && oj < n) {
+            const double g = T[r][c];
+            K64[oi * ldk + oj] = g;
+            if (W32) K32[oi * ldk + oj] = (float)g;
+        }
+    }
+}
+
+__global__ void k_diag(const double* __restrict__ Q, int64_t n, int d, double scale, double lambda,
+                       double* __restrict__ diag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s = fma(Q[i * d + k], Q[i * d + k], s);
+    diag[i] = exp(scale * s) + lambda;
+}
+
+// Split q * sqrt(scale * log2(e)) into bf16 high and low parts (zero-padded to
+// dpad columns).  Folding the scale and log2(e) into the operands lets the
+// matrix-free kernels feed the tensor-core logits straight into ex2.
+__global__ void k_split_bf16(const double* __restrict__ Q, int64_t n, int d, int dpad, double fold,
+                             uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                             float* __restrict__ q32) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * dpad) return;
+    const int64_t i = idx / dpad;
+    const int k = (int)(idx % dpad);
+    const double q = (k < d) ? Q[i * d + k] * fold : 0.0;
+    const __nv_bfloat16 h = __double2bfloat16(q);
+    const __nv_bfloat16 l = __double2bfloat16(q - (double)__bfloat162float(h));
+    hi[idx] = __bfloat16_as_ushort(h);
+    lo[idx] = __bfloat16_as_ushort(l);
+    if (k < d) q32[i * d + k] = (float)Q[i * d + k];
+}
+
+}  // namespace
+
+laker_status build_operator(laker_ctx* ctx, laker_op* op) {
+    const int64_t n = op->n;
+    const int d = op->d;
+    op->ldk = (n + 3) / 4 * 4;
+    op->dpad = (d + 15) / 16 * 16;
+    // float32 copy of G: the materialised FP32 operator, and the float32 GEMM of
+    // the preconditioner fit for every non-FP64 operator
+    const bool need32 = (op->precision != LAKER_FP64);
+    const size_t kbytes64 = (size_t)n * op->ldk * sizeof(double);
+    laker_status st;
+    if ((st = lk_malloc(ctx, (void**)&op->K64, kbytes64)) != LAKER_OK) return st;
+    if (need32 && (st = lk_malloc(ctx, (void**)&op->K32, (size_t)n * op->ldk * sizeof(float))) != LAKER_OK)
+        return st;
+    if ((st = lk_malloc(ctx, (void**)&op->diagA, (size_t)n * sizeof(double))) != LAKER_OK) return st;
+    if (op->ldk > n) {
+        LK_CUDA(ctx, cudaMemset2DAsync(op->K64 + n, op->ldk * sizeof(double), 0,
+                                       (op->ldk - n) * sizeof(double), n, ctx->stream));
+        if (need32)
+            LK_CUDA(ctx, cudaMemset2DAsync(op->K32 + n, op->ldk * sizeof(float), 0,
+                                           (op->ldk - n) * sizeof(float), n, ctx->stream));
+    }
+    const int nt = (int)((n + BT - 1) / BT);
+    const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
+    if (need32)
+        k_build_sym<true><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64,
+                                                                    op->K32, op->ldk, nt);
+    else
+        k_build_sym<false><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64,
+                                                                     nullptr, op->ldk, nt);
+    LK_LAUNCHED(ctx);
+    k_diag<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->lambda,
+                                                                 op->diagA);
+    LK_LAUNCHED(ctx);
+    if (op->precision == LAKER_BF16X3) {
+        if (!(op->scale > 0.0))
+            return set_error(ctx, LAKER_ERR_ARG, "BF16X3 operator needs scale > 0");
+        const size_t e = (size_t)n * op->dpad;
+        if ((st = lk_malloc(ctx, (void**)&op->Qhi, e * 2)) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&op->Qlo, e * 2)) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&op->Q32, (size_t)n * d * sizeof(float))) != LAKER_OK) return st;
+        const double fold = std::sqrt(op->scale * 1.4426950408889634);
+        k_split_bf16<<<(unsigned)((e + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->dpad, fold,
+                                                                           op->Qhi, op->Qlo, op->Q32);
+        LK_LAUNCHED(ctx);
+    }
+    return LAKER_OK;
+}

@@ -1,0 +1,68 @@
+// Device helpers shared by the CUDA kernels of liblaker (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "laker_internal.h"
+
+namespace lk {
+
+constexpr int WARP = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block sum; every thread receives the result.  `red` needs
+// blockDim.x / 32 slots.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T s = (threadIdx.x < nw) ? red[threadIdx.x] : T(0);
+    if (wid == 0) s = warp_sum(s);
+    if (threadIdx.x == 0) red[0] = s;
+    __syncthreads();
+    s = red[0];
+    __syncthreads();
+    return s;
+}
+
+// Last-block-done ticket.  Call after thread 0 has written this block's
+// partial; returns true in exactly one block, which may then read every
+// block's partial (with ld.cg) and must reset the ticket.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// Sum of partials[0..count) in a fixed order by one block.
+__device__ __forceinline__ double sum_partials(const double* partials, int count, double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += __ldcg(partials + i);
+    return block_sum(s, red);
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+}  // namespace lk

@@ -1,0 +1,621 @@
+// Preconditioner learning on GB300 (Sec. IV-B..IV-D; Algorithm 1, learning stage).
+//
+// Representation.  With Sigma_0 = I, every F_gamma(Sigma_t) is a weighted sum of
+// the u_k u_k^T plus a multiple of I, and shrinkage and trace normalisation keep
+// that form, so every iterate is exactly
+//        Sigma_t = c_t I + U diag(D_t) U^T,    U = [u_1 .. u_Nr]  (unit columns).
+// A CCCP update therefore needs only the N_r quadratic forms
+//        q_k = u_k^T Sigma_t^-1 u_k = (M_kk - |Y_{:,k}|^2) / c,
+// with M = U^T U, C = c I + D^1/2 M D^1/2 = L L^T and Y = L^-1 D^1/2 M (Woodbury).
+// Y is obtained for free by running the blocked Cholesky on the bordered panel
+// [C ; M D^1/2] (2 N_r x N_r): the lower half of the factor is Y^T.
+// P = Sigma_*^-1/2 = c^-1/2 I + U B U^T with
+//        B = D^1/2 V diag(f(Lambda)) V^T D^1/2,  D^1/2 M D^1/2 = V Lambda V^T,
+//        f(l) = ((c + l)^-1/2 - c^-1/2) / l  (evaluated without cancellation),
+// found by a parallel cyclic Jacobi eigensolver; the apply uses W = U B.
+// All small dense algebra is float64 and spread over many thread blocks (GB300's
+// float64 pipe is slow per SM); every reduction has a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "laker_device.cuh"
+
+namespace {
+
+constexpr int NB = 32;   // panel / tile edge of the small dense kernels
+
+// ---------------------------------------------------------------------------
+// Generic SIMT GEMM with split-K:  C_z = op(A) op(B) over k in split z.
+// op(A)(i,k) = TA ? A[k*lda+i] : A[i*lda+k];  op(B)(k,j) = TB ? B[j*ldb+k] : B[k*ldb+j]
+// ---------------------------------------------------------------------------
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+k_gemm(int64_t M, int64_t N, int64_t Kd, const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+       int64_t ldb, T* __restrict__ C, int64_t ldc, int64_t kchunk) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk, ke = min(Kd, kb + kchunk);
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            int r, kk;
+            if (TA) { kk = idx / BM; r = idx % BM; } else { r = idx / BK; kk = idx % BK; }
+            const int64_t gi = i0 + r, gk = k0 + kk;
+            T v = T(0);
+            if (gi < M && gk < ke) v = TA ? A[gk * lda + gi] : A[gi * lda + gk];
+            As[kk][r] = v;
+        }
+        for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+            int c, kk;
+            if (TB) { c = idx / BK; kk = idx % BK; } else { kk = idx / BN; c = idx % BN; }
+            const int64_t gj = j0 + c, gk = k0 + kk;
+            T v = T(0);
+            if (gj < N && gk < ke) v = TB ? B[gj * ldb + gk] : B[gk * ldb + gj];
+            Bs[kk][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty + 16 * u]; b[u] = Bs[kk][tx + 16 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    T* Cz = C + (int64_t)blockIdx.z * M * ldc;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t gi = i0 + ty + 16 * u;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t gj = j0 + tx + 16 * v;
+            if (gi < M && gj < N) Cz[gi * ldc + gj] = acc[u][v];
+        }
+    }
+}
+
+// out = sum_z parts[z] (fixed order) + lam * X   (X may be null), in float64.
+template <typename T>
+__global__ void k_reduce_splits(int64_t M, int64_t N, int nz, const T* __restrict__ parts, int64_t ldp,
+                                double lam, const double* __restrict__ X, int64_t ldx, double* __restrict__ out,
+                                int64_t ldo) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * N) return;
+    const int64_t i = idx / N, j = idx % N;
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += (double)parts[(int64_t)z * M * ldp + i * ldp + j];
+    if (X) s = fma(lam, X[i * ldx + j], s);
+    out[i * ldo + j] = s;
+}
+
+template <typename T>
+laker_status gemm(laker_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t Kd, const T* A, int64_t lda,
+                  const T* B, int64_t ldb, double lam, const double* X, int64_t ldx, double* out, int64_t ldo) {
+    const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    int64_t want = std::max<int64_t>(1, (4 * ctx->num_sms + tiles - 1) / tiles);
+    int64_t kchunk = (Kd + want - 1) / want;
+    kchunk = std::max<int64_t>(64, (kchunk + 15) / 16 * 16);
+    const int nz = (int)((Kd + kchunk - 1) / kchunk);
+    T* parts = nullptr;
+    laker_status st = lk_malloc(ctx, (void**)&parts, (size_t)nz * M * N * sizeof(T));
+    if (st != LAKER_OK) return st;
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)nz);
+    if (!ta && !tb) k_gemm<T, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
+    else if (ta && !tb) k_gemm<T, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
+    else if (!ta && tb) k_gemm<T, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
+    else k_gemm<T, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
+    LK_LAUNCHED(ctx);
+    k_reduce_splits<T><<<(unsigned)((M * N + 255) / 256), 256, 0, ctx->stream>>>(M, N, nz, parts, N, lam, X, ldx,
+                                                                                  out, ldo);
+    LK_LAUNCHED(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(parts);
+    return LAKER_OK;
+}
+
+__global__ void k_to_float(int64_t count, const double* __restrict__ x, float* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) y[i] = (float)x[i];
+}
+
+// u_bar_k = u_k / |u_k|  (columns of an n x n_r row-major matrix), fixed-order norms.
+__global__ void k_colnorm(int64_t n, int n_r, const double* __restrict__ U, double* __restrict__ inv) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = U[i * n_r + k];
+        s = fma(v, v, s);
+    }
+    s = lk::block_sum(s, red);
+    if (threadIdx.x == 0) inv[k] = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+}
+__global__ void k_colscale(int64_t n, int n_r, double* __restrict__ U, const double* __restrict__ inv) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n_r) return;
+    U[idx] *= inv[idx % n_r];
+}
+
+// ---------------------------------------------------------------------------
+// CCCP state and kernels (padded size NP = round_up(N_r, 32))
+// ---------------------------------------------------------------------------
+struct CccpState {
+    double c;          // current isotropic coefficient
+    double change;     // relative Frobenius change of the last update
+    double trace_tau;  // tr(Sigma~)/n of the last update
+    int iter;
+    int converged;
+    int status;        // 0 ok, else laker_status
+    unsigned int ticket;
+};
+
+// A (2NP x NP): top = C = cI + D^1/2 M D^1/2 (padding: identity), bottom = M D^1/2.
+__global__ void k_cccp_form(int NP, int nr, const double* __restrict__ M, const double* __restrict__ D,
+                            const CccpState* st, double* __restrict__ A) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)2 * NP * NP) return;
+    const int row = (int)(idx / NP), col = (int)(idx % NP);
+    const double c = st->c;
+    double v = 0.0;
+    if (row < NP) {
+        const int j = row;
+        if (j < nr && col < nr) v = sqrt(D[j]) * M[(int64_t)j * nr + col] * sqrt(D[col]);
+        if (j == col) v += (j < nr) ? c : 1.0;
+    } else {
+        const int k = row - NP;
+        if (k < nr && col < nr) v = M[(int64_t)k * nr + col] * sqrt(D[col]);
+    }
+    A[idx] = v;
+}
+
+// Cholesky of the diagonal tile jb (one block of NB x NB threads).
+__global__ void __launch_bounds__(NB * NB) k_potrf_diag(double* __restrict__ A, int lda, int jb, int* status) {
+    __shared__ double T[NB][NB + 1];
+    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
+    const int64_t g0 = (int64_t)jb * NB;
+    T[r][c] = A[(g0 + r) * lda + g0 + c];
+    __syncthreads();
+    for (int j = 0; j < NB; ++j) {
+        if (r == j && c == j) {
+            const double d = T[j][j];
+            if (!(d > 0.0) || !isfinite(d)) { *status = LAKER_ERR_NOT_SPD; T[j][j] = 1.0; }
+            else T[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (c == j && r > j) T[r][j] /= T[j][j];
+        __syncthreads();
+        if (r > j && c > j && c <= r) T[r][c] = fma(-T[r][j], T[c][j], T[r][c]);
+        __syncthreads();
+    }
+    A[(g0 + r) * lda + g0 + c] = (c <= r) ? T[r][c] : 0.0;
+}
+
+// Row blocks ib in (jb, nrb): A_ib,jb <- A_ib,jb L_jb^-T (one block per row block, warp per row).
+__global__ void __launch_bounds__(NB * NB) k_trsm_panel(double* __restrict__ A, int lda, int jb) {
+    __shared__ double L[NB][NB + 1];
+    const int ib = jb + 1 + blockIdx.x;
+    const int lane = threadIdx.x % NB, row = threadIdx.x / NB;
+    const int64_t g0 = (int64_t)jb * NB;
+    L[row][lane] = A[(g0 + row) * lda + g0 + lane];
+    __syncthreads();
+    const int64_t gr = (int64_t)ib * NB + row;
+    const double a = A[gr * lda + g0 + lane];
+    double acc = 0.0, x = 0.0;
+    for (int j = 0; j < NB; ++j) {
+        double xj = 0.0;
+        if (lane == j) { x = (a - acc) / L[j][j]; xj = x; }
+        xj = __shfl_sync(0xffffffffu, xj, j);
+        if (lane > j) acc = fma(L[lane][j], xj, acc);
+    }
+    A[gr * lda + g0 + lane] = x;
+}
+
+// Trailing update after panel jb: A_ib,kb -= A_ib,jb A_kb,jb^T over
+// top tiles (jb < kb <= ib < ncb) and bottom tiles (ncb <= ib < 2 ncb, jb < kb < ncb).
+__global__ void __launch_bounds__(256) k_syrk_update(double* __restrict__ A, int lda, int jb, int ncb) {
+    const int m = ncb - jb - 1;
+    const int top = m * (m + 1) / 2;
+    int t = blockIdx.x, ib, kb;
+    if (t < top) {
+        int rI = 0;
+        while (t >= rI + 1) { t -= rI + 1; ++rI; }
+        ib = jb + 1 + rI;
+        kb = jb + 1 + t;
+    } else {
+        t -= top;
+        ib = ncb + t / m;
+        kb = jb + 1 + t % m;
+    }
+    __shared__ double X[NB][NB + 1], Y[NB][NB + 1];
+    const int64_t cj = (int64_t)jb * NB;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) {
+        const int r = idx / NB, c = idx % NB;
+        X[r][c] = A[((int64_t)ib * NB + r) * lda + cj + c];
+        Y[r][c] = A[((int64_t)kb * NB + r) * lda + cj + c];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int k = 0; k < NB; ++k) {
+        const double x0 = X[ty][k], x1 = X[ty + 16][k];
+        const double y0 = Y[tx][k], y1 = Y[tx + 16][k];
+        acc[0][0] = fma(x0, y0, acc[0][0]);
+        acc[0][1] = fma(x0, y1, acc[0][1]);
+        acc[1][0] = fma(x1, y0, acc[1][0]);
+        acc[1][1] = fma(x1, y1, acc[1][1]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int64_t gi = (int64_t)ib * NB + ty + 16 * u, gk = (int64_t)kb * NB + tx + 16 * v;
+            A[gi * lda + gk] -= acc[u][v];
+        }
+}
+
+// q_k = (M_kk - |row k of the bottom factor|^2) / c   (warp per k)
+__global__ void k_cccp_q(int NP, int nr, const double* __restrict__ A, const double* __restrict__ M,
+                         const CccpState* st, double* __restrict__ q) {
+    const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (k >= nr) return;
+    const double* row = A + (int64_t)(NP + k) * NP;
+    double s = 0.0;
+    for (int j = lane; j < NP; j += 32) s = fma(row[j], row[j], s);
+    s = lk::warp_sum(s);
+    if (lane == 0) q[k] = (M[(int64_t)k * nr + k] - s) / st->c;
+}
+
+// New weights: Dn = (1-rho) w / tau, cn = ((1-rho) b + rho) / tau with
+// w_k = (n/N_r) / (q_k + eps) / (1 + gamma/n), b = gamma / (1 + gamma/n),
+// tau = tr(Sigma~)/n (Eqs. kernel_shrinkage_cccp_F/_Sigma/_normalization).
+__global__ void k_cccp_weights(int nr, double n, double gamma, double rho, double eps, const double* __restrict__ q,
+                               const double* __restrict__ M, double* __restrict__ Dn, CccpState* st, double* cn_out) {
+    __shared__ double red[32];
+    const double scale = (n / nr) / (1.0 + gamma / n);
+    double tr = 0.0;
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        const double wk = (1.0 - rho) * scale / (q[k] + eps);
+        Dn[k] = wk;
+        tr = fma(wk, M[(int64_t)k * nr + k], tr);
+    }
+    tr = lk::block_sum(tr, red);
+    const double ct = (1.0 - rho) * gamma / (1.0 + gamma / n) + rho;
+    const double tau = (tr + n * ct) / n;
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) Dn[k] /= tau;
+    if (threadIdx.x == 0) {
+        *cn_out = ct / tau;
+        st->trace_tau = tau;
+    }
+}
+
+// Relative Frobenius change |S_new - S_old|_F / |S_old|_F with S = cI + U D U^T:
+//   |xI + U E U^T|_F^2 = n x^2 + 2 x sum_k E_k M_kk + sum_kl E_k E_l M_kl^2.
+// Block per row k of the double sums; the last block finalises and commits the state.
+__global__ void k_cccp_commit(int nr, double n, double tol, const double* __restrict__ M,
+                              double* __restrict__ D, const double* __restrict__ Dn, const double* cn,
+                              CccpState* st, double* __restrict__ partials) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    double sd = 0.0, so = 0.0;
+    const double dk = Dn[k] - D[k], ok = D[k];
+    for (int l = threadIdx.x; l < nr; l += blockDim.x) {
+        const double m2 = M[(int64_t)k * nr + l] * M[(int64_t)k * nr + l];
+        sd = fma(dk * (Dn[l] - D[l]), m2, sd);
+        so = fma(ok * D[l], m2, so);
+    }
+    sd = lk::block_sum(sd, red);
+    so = lk::block_sum(so, red);
+    if (threadIdx.x == 0) {
+        partials[2 * k] = sd;
+        partials[2 * k + 1] = so;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double qd = 0.0, qo = 0.0, td = 0.0, to = 0.0;
+    for (int l = threadIdx.x; l < nr; l += blockDim.x) {
+        qd += __ldcg(partials + 2 * l);
+        qo += __ldcg(partials + 2 * l + 1);
+        const double mkk = M[(int64_t)l * nr + l];
+        td = fma(Dn[l] - D[l], mkk, td);
+        to = fma(D[l], mkk, to);
+    }
+    qd = lk::block_sum(qd, red);
+    qo = lk::block_sum(qo, red);
+    td = lk::block_sum(td, red);
+    to = lk::block_sum(to, red);
+    const double c_old = st->c, c_new = *cn;
+    const double dc = c_new - c_old;
+    const double num = n * dc * dc + 2.0 * dc * td + qd;
+    const double den = n * c_old * c_old + 2.0 * c_old * to + qo;
+    const double change = sqrt(fmax(num, 0.0) / den);
+    __syncthreads();
+    for (int l = threadIdx.x; l < nr; l += blockDim.x) D[l] = Dn[l];
+    if (threadIdx.x == 0) {
+        st->c = c_new;
+        st->change = change;
+        st->iter += 1;
+        if (!isfinite(change)) st->status = LAKER_ERR_NONFINITE;
+        st->converged = (change <= tol) ? 1 : 0;
+        st->ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Parallel cyclic Jacobi eigensolver (round-robin ordering), float64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int rr_player(int pos, int round, int m) {
+    return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1);
+}
+
+// One block per pair: compute the rotation from the 2x2 block and rotate rows p, q.
+__global__ void k_jacobi_rows(double* __restrict__ S, int m, int round, double* __restrict__ cs) {
+    const int k = blockIdx.x;
+    int p = rr_player(k, round, m), q = rr_player(m - 1 - k, round, m);
+    if (p > q) { const int t = p; p = q; q = t; }
+    __shared__ double c_s[2];
+    if (threadIdx.x == 0) {
+        const double app = S[(int64_t)p * m + p], aqq = S[(int64_t)q * m + q], apq = S[(int64_t)p * m + q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0 && fabs(apq) > 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+        }
+        c_s[0] = c;
+        c_s[1] = s;
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+    }
+    __syncthreads();
+    const double c = c_s[0], s = c_s[1];
+    if (s == 0.0) return;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const double a = S[(int64_t)p * m + j], b = S[(int64_t)q * m + j];
+        S[(int64_t)p * m + j] = c * a - s * b;
+        S[(int64_t)q * m + j] = s * a + c * b;
+    }
+}
+
+// Rotate columns p, q of S and V for every pair; grid over rows.
+__global__ void k_jacobi_cols(double* __restrict__ S, double* __restrict__ V, int m, int round,
+                              const double* __restrict__ cs) {
+    const int i = blockIdx.x;
+    for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
+        int p = rr_player(k, round, m), q = rr_player(m - 1 - k, round, m);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        double* Si = S + (int64_t)i * m;
+        const double a = Si[p], b = Si[q];
+        Si[p] = c * a - s * b;
+        Si[q] = s * a + c * b;
+        if (i == p) Si[q] = 0.0;
+        if (i == q) Si[p] = 0.0;
+        double* Vi = V + (int64_t)i * m;
+        const double va = Vi[p], vb = Vi[q];
+        Vi[p] = c * va - s * vb;
+        Vi[q] = s * va + c * vb;
+    }
+}
+
+// off-diagonal and total squared Frobenius norms -> out[0], out[1] (single block)
+__global__ void k_offdiag(const double* __restrict__ S, int m, double* out) {
+    __shared__ double red[32];
+    double off = 0.0, tot = 0.0;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
+        const double v = S[idx];
+        tot = fma(v, v, tot);
+        if (idx / m != idx % m) off = fma(v, v, off);
+    }
+    off = lk::block_sum(off, red);
+    tot = lk::block_sum(tot, red);
+    if (threadIdx.x == 0) { out[0] = off; out[1] = tot; }
+}
+
+__global__ void k_eye(double* V, int m) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < (int64_t)m * m) V[idx] = (idx / m == idx % m) ? 1.0 : 0.0;
+}
+
+// S = D^1/2 M D^1/2 padded to m x m
+__global__ void k_scaled_gram(int m, int nr, const double* __restrict__ M, const double* __restrict__ D,
+                              double* __restrict__ S) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    S[idx] = (i < nr && j < nr) ? sqrt(D[i]) * M[(int64_t)i * nr + j] * sqrt(D[j]) : 0.0;
+}
+
+// X = V diag(f(Lambda)),  f(l) = ((c+l)^-1/2 - c^-1/2)/l = -1 / (sqrt(c+l) sqrt(c) (sqrt(c+l) + sqrt(c)))
+__global__ void k_vf(int m, const double* __restrict__ S, const double* __restrict__ V, double c,
+                     double* __restrict__ X) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    const int j = (int)(idx % m);
+    const double l = fmax(S[(int64_t)j * m + j], 0.0);
+    const double a = sqrt(c + l), b = sqrt(c);
+    X[idx] = V[idx] * (-1.0 / (a * b * (a + b)));
+}
+
+// B = D^1/2 B0 D^1/2 restricted to nr x nr
+__global__ void k_scale_B(int m, int nr, const double* __restrict__ B0, const double* __restrict__ D,
+                          double* __restrict__ B) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nr * nr) return;
+    const int i = (int)(idx / nr), j = (int)(idx % nr);
+    B[idx] = sqrt(D[i]) * B0[(int64_t)i * m + j] * sqrt(D[j]);
+}
+
+unsigned gsz(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b); }
+
+}  // namespace
+
+laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma, double rho,
+                      double eps, int max_iter, double tol, laker_precond* P, laker_fit_info* info) {
+    const int64_t n = op->n;
+    const int nr = n_r;
+    const int NP = (nr + NB - 1) / NB * NB;
+    const int ncb = NP / NB;
+    laker_status st;
+    cudaStream_t s = ctx->stream;
+    // ---- random directions u_k = (lambda I + G) z_k, normalised (Eq. random_directions)
+    double* U64 = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&U64, (size_t)n * nr * sizeof(double))) != LAKER_OK) return st;
+    P->U64 = U64;
+    if (op->precision == LAKER_FP64) {
+        st = gemm<double>(ctx, false, false, n, nr, n, op->K64, op->ldk, Z, nr, op->lambda, Z, nr, U64, nr);
+    } else {
+        float* Z32 = nullptr;
+        if ((st = lk_malloc(ctx, (void**)&Z32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, Z, Z32);
+        LK_LAUNCHED(ctx);
+        st = gemm<float>(ctx, false, false, n, nr, n, op->K32, op->ldk, Z32, nr, op->lambda, Z, nr, U64, nr);
+        cudaFree(Z32);
+    }
+    if (st != LAKER_OK) return st;
+    double* tmpv = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&tmpv, (size_t)4 * NP * sizeof(double))) != LAKER_OK) return st;
+    k_colnorm<<<nr, 256, 0, s>>>(n, nr, U64, tmpv);
+    LK_LAUNCHED(ctx);
+    k_colscale<<<gsz(n * nr), 256, 0, s>>>(n, nr, U64, tmpv);
+    LK_LAUNCHED(ctx);
+    // ---- Gram M = U^T U
+    double *M = nullptr, *A = nullptr, *D = nullptr, *Dn = nullptr, *q = nullptr, *partials = nullptr, *cn = nullptr;
+    CccpState* dst = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&M, (size_t)nr * nr * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&A, (size_t)2 * NP * NP * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&D, (size_t)NP * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&Dn, (size_t)NP * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&q, (size_t)NP * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&partials, (size_t)2 * NP * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&cn, sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&dst, sizeof(CccpState))) != LAKER_OK) return st;
+    if ((st = gemm<double>(ctx, true, false, nr, nr, n, U64, nr, U64, nr, 0.0, nullptr, 0, M, nr)) != LAKER_OK)
+        return st;
+    // ---- shrinkage-regularised CCCP
+    if (rho < 0.0) rho = (nr >= n) ? 1e-3 : std::min(0.5, std::max(1e-3, gamma * (1.0 - (double)nr / n)));
+    CccpState h{};
+    h.c = 1.0;
+    LK_CUDA(ctx, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    LK_CUDA(ctx, cudaMemsetAsync(D, 0, NP * sizeof(double), s));
+    int* dstatus = &dst->status;
+    for (int it = 0; it < max_iter; ++it) {
+        k_cccp_form<<<gsz((int64_t)2 * NP * NP), 256, 0, s>>>(NP, nr, M, D, dst, A);
+        LK_LAUNCHED(ctx);
+        for (int jb = 0; jb < ncb; ++jb) {
+            k_potrf_diag<<<1, NB * NB, 0, s>>>(A, NP, jb, dstatus);
+            LK_LAUNCHED(ctx);
+            const int below = 2 * ncb - jb - 1;
+            k_trsm_panel<<<below, NB * NB, 0, s>>>(A, NP, jb);
+            LK_LAUNCHED(ctx);
+            const int m = ncb - jb - 1;
+            const int tiles = m * (m + 1) / 2 + ncb * m;
+            if (tiles > 0) {
+                k_syrk_update<<<tiles, 256, 0, s>>>(A, NP, jb, ncb);
+                LK_LAUNCHED(ctx);
+            }
+        }
+        k_cccp_q<<<(nr + 7) / 8, 256, 0, s>>>(NP, nr, A, M, dst, q);
+        LK_LAUNCHED(ctx);
+        k_cccp_weights<<<1, 512, 0, s>>>(nr, (double)n, gamma, rho, eps, q, M, Dn, dst, cn);
+        LK_LAUNCHED(ctx);
+        k_cccp_commit<<<nr, 128, 0, s>>>(nr, (double)n, tol, M, D, Dn, cn, dst, partials);
+        LK_LAUNCHED(ctx);
+        LK_CUDA(ctx, cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        if (h.status != 0 || h.converged) break;
+    }
+    // ---- P = Sigma^-1/2 via the eigendecomposition of D^1/2 M D^1/2
+    double *Sm = nullptr, *V = nullptr, *cs = nullptr, *X = nullptr, *B0 = nullptr, *B = nullptr, *nrm = nullptr;
+    const int m = NP;   // even
+    if ((st = lk_malloc(ctx, (void**)&Sm, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&V, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&cs, (size_t)m * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&X, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&B0, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&B, (size_t)nr * nr * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&nrm, 2 * sizeof(double))) != LAKER_OK) return st;
+    k_scaled_gram<<<gsz((int64_t)m * m), 256, 0, s>>>(m, nr, M, D, Sm);
+    LK_LAUNCHED(ctx);
+    k_eye<<<gsz((int64_t)m * m), 256, 0, s>>>(V, m);
+    LK_LAUNCHED(ctx);
+    // one sweep = m-1 rounds, captured once into a graph
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    LK_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < m - 1; ++r) {
+        k_jacobi_rows<<<m / 2, 128, 0, s>>>(Sm, m, r, cs);
+        k_jacobi_cols<<<m, 128, 0, s>>>(Sm, V, m, r, cs);
+    }
+    k_offdiag<<<1, 1024, 0, s>>>(Sm, m, nrm);
+    LK_CUDA(ctx, cudaStreamEndCapture(s, &g));
+    LK_CUDA(ctx, cudaGraphInstantiate(&ge, g, 0));
+    double hn[2] = {0, 0};
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        LK_CUDA(ctx, cudaGraphLaunch(ge, s));
+        ctx->launches += 2 * (m - 1) + 1;
+        LK_CUDA(ctx, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        if (!(hn[0] > 1e-30 * hn[1])) break;
+    }
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    k_vf<<<gsz((int64_t)m * m), 256, 0, s>>>(m, Sm, V, h.c, X);
+    LK_LAUNCHED(ctx);
+    if ((st = gemm<double>(ctx, false, true, m, m, m, X, m, V, m, 0.0, nullptr, 0, B0, m)) != LAKER_OK) return st;
+    k_scale_B<<<gsz((int64_t)nr * nr), 256, 0, s>>>(m, nr, B0, D, B);
+    LK_LAUNCHED(ctx);
+    double* W64 = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&W64, (size_t)n * nr * sizeof(double))) != LAKER_OK) return st;
+    if ((st = gemm<double>(ctx, false, false, n, nr, nr, U64, nr, B, nr, 0.0, nullptr, 0, W64, nr)) != LAKER_OK)
+        return st;
+    P->W64 = W64;
+    P->kind = PRECOND_CCCP;
+    P->n = n;
+    P->n_r = nr;
+    P->c = h.c;
+    P->cinvsqrt = 1.0 / std::sqrt(h.c);
+    if ((st = lk_malloc(ctx, (void**)&P->D, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMemcpyAsync(P->D, D, nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (op->precision != LAKER_FP64) {
+        if ((st = lk_malloc(ctx, (void**)&P->U32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, U64, P->U32);
+        LK_LAUNCHED(ctx);
+        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, W64, P->W32);
+        LK_LAUNCHED(ctx);
+    }
+    LK_CUDA(ctx, cudaStreamSynchronize(s));
+    for (void* ptr : {(void*)tmpv, (void*)M, (void*)A, (void*)D, (void*)Dn, (void*)q, (void*)partials, (void*)cn,
+                      (void*)dst, (void*)Sm, (void*)V, (void*)cs, (void*)X, (void*)B0, (void*)B, (void*)nrm})
+        cudaFree(ptr);
+    if (info) {
+        info->iterations = h.iter;
+        info->converged = h.converged;
+        info->c = h.c;
+        info->rho = rho;
+        info->change = h.change;
+        info->status = h.status;
+    }
+    if (h.status != 0) return set_error(ctx, (laker_status)h.status, "CCCP factorisation failed");
+    return LAKER_OK;
+}

@@ -1,0 +1,118 @@
+// Host-side internals shared by the CUDA translation units of liblaker.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/laker.h"
+
+// Device-resident PCG scalars.  All reductions that feed them are done in a
+// fixed order, so a solve is bit-reproducible for a given launch shape.
+struct PcgScalars {
+    double rz;          // r^T z of the current iterate
+    double pAp;         // p^T (lambda I + G) p
+    double delta;       // step length
+    double beta;        // conjugation coefficient
+    double rr;          // |r|^2 of the recursive residual
+    double yy;          // |y|^2
+    double tol2yy;      // tol^2 |y|^2
+    double rr_true;     // |y - A alpha|^2 at the last true-residual step
+    int converged;      // 0 running, 1 converged, 2 breakdown, 3 max iterations
+    int iters;          // operator products so far
+    int need_true;      // the next true-residual step must run
+    int true_count;     // true residuals computed
+    int max_iter;
+    int refine_every;   // 0 = never replace the residual
+    int pad0, pad1;
+    unsigned int ticket[8];
+};
+
+struct laker_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    int num_sms = 0;
+    int64_t launches = 0;
+    std::string last_error;
+};
+
+struct laker_op {
+    laker_ctx* ctx = nullptr;
+    int64_t n = 0;
+    int d = 0;
+    int dpad = 0;             // d rounded up to a multiple of 16 (bf16 operands)
+    int64_t ldk = 0;          // leading dimension of materialised G (multiple of 4)
+    double scale = 1.0;
+    double lambda = 0.0;
+    int precision = LAKER_FP64;
+    int variant = LAKER_MATERIALISED;
+    double* Q64 = nullptr;    // n x d
+    uint16_t* Qhi = nullptr;  // n x dpad bf16, high part of Q * sqrt(scale * log2 e)
+    uint16_t* Qlo = nullptr;  // n x dpad bf16, low part
+    float* Q32 = nullptr;     // n x d float copy
+    double* K64 = nullptr;    // n x ldk, G in float64
+    float* K32 = nullptr;     // n x ldk, G rounded to float
+    double* diagA = nullptr;  // n, lambda + G_ii
+};
+
+enum PrecondKind { PRECOND_IDENTITY = 0, PRECOND_JACOBI = 1, PRECOND_CCCP = 2 };
+
+struct laker_precond {
+    laker_ctx* ctx = nullptr;
+    int kind = PRECOND_IDENTITY;
+    int64_t n = 0;
+    int n_r = 0;
+    double c = 1.0;           // Sigma_* = c I + U diag(D) U^T
+    double cinvsqrt = 1.0;    // c^{-1/2}
+    double* D = nullptr;      // n_r
+    double* U64 = nullptr;    // n x n_r, unit columns u_bar_k
+    double* W64 = nullptr;    // n x n_r, W = U B with P = c^{-1/2} I + W U^T
+    float* U32 = nullptr;
+    float* W32 = nullptr;
+    double* dinv = nullptr;   // Jacobi: 1/diag(A)
+    bool use32 = false;       // apply in float32 (mixed solves)
+};
+
+// ---- error plumbing ------------------------------------------------------
+laker_status set_error(laker_ctx* ctx, laker_status st, const std::string& msg);
+#define LK_CUDA(ctx, call)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return set_error((ctx), LAKER_ERR_CUDA,                                 \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+#define LK_LAUNCHED(ctx)                                                            \
+    do {                                                                            \
+        (ctx)->launches++;                                                          \
+        cudaError_t e_ = cudaGetLastError();                                        \
+        if (e_ != cudaSuccess)                                                      \
+            return set_error((ctx), LAKER_ERR_CUDA,                                 \
+                             std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+laker_status lk_malloc(laker_ctx* ctx, void** p, size_t bytes);
+
+// ---- translation-unit entry points ---------------------------------------
+// laker_build.cu
+laker_status build_operator(laker_ctx* ctx, laker_op* op);
+laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
+laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
+// laker_pcg.cu
+laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
+                       const double* y, double* alpha, double tol, int max_iter,
+                       int refine_every, laker_solve_info* info);
+laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
+// laker_fit.cu
+laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
+                      double gamma, double rho, double eps, int max_iter, double tol,
+                      laker_precond* P, laker_fit_info* info);
+// laker_map.cu
+laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                      const double* alpha, double* out);
+// laker_mf.cu (matrix-free operator)
+laker_status mf_matvec_launch(laker_ctx* ctx, const laker_op* op, const double* pin,
+                              const double* z, double* pout, double* w, PcgScalars* sc,
+                              double* partials, int fuse_p, float* pbuf, float* wbuf);

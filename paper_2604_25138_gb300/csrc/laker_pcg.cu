@@ -1,0 +1,686 @@
+// Preconditioned conjugate gradient on GB300 (Sec. IV-E, Algorithm 1, PCG stage).
+//
+// One PCG iteration is four kernels, all reading their scalars from device
+// memory so that a block of iterations is captured once into a CUDA graph and
+// replayed; the host only polls a convergence word between replays:
+//
+//   MV   p = z + beta p_old (fused prologue), w = (lambda I + G) p,
+//        p^T w  -> last block: delta = r.z / p^T A p          (HBM-bound stream of G)
+//   UPD  alpha += delta p, r -= delta w, |r|^2, U^T r partials
+//        -> last block: stop test, t = U^T r
+//   [TR1, TR2]  only when a float64-accurate residual is due (mixed forms):
+//        w2 = (lambda I + G64) alpha, r = y - w2, stop test on the true residual
+//   PRE  z = P r, r^T z -> last block: beta = r.z_new / r.z_old
+//
+// All cross-block sums go through per-block partials reduced in a fixed order
+// by the last block to finish (atomic ticket), so results are deterministic.
+#include <cmath>
+#include <vector>
+
+#include "laker_device.cuh"
+
+namespace {
+
+constexpr int MV_THREADS = 512;
+constexpr int VEC_THREADS = 256;
+
+enum Gate { GATE_NONE = 0, GATE_RUNNING = 1, GATE_TRUE = 2 };
+
+__device__ __forceinline__ bool gated_out(const PcgScalars* sc, int gate) {
+    if (gate == GATE_NONE || sc == nullptr) return false;
+    const int conv = *(volatile const int*)&sc->converged;
+    if (conv != 0) return true;
+    if (gate == GATE_TRUE) return *(volatile const int*)&sc->need_true == 0;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// MV: materialised operator.  Block b owns rows [r0, r1); p is staged in
+// shared memory column chunk by column chunk (converted to the storage type of
+// G), each warp streams whole rows of G with 16-byte loads and keeps the
+// running row sums in shared memory across chunks.
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ T dot16(const typename Vec16<T>::type& a, const T* p);
+template <>
+__device__ __forceinline__ float dot16<float>(const float4& a, const float* p) {
+    const float4 b = *reinterpret_cast<const float4*>(p);
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+template <>
+__device__ __forceinline__ double dot16<double>(const double2& a, const double* p) {
+    const double2 b = *reinterpret_cast<const double2*>(p);
+    return fma(a.x, b.x, a.y * b.y);
+}
+
+template <typename T, bool STREAM>
+__device__ __forceinline__ typename Vec16<T>::type ldk16(const typename Vec16<T>::type* p) {
+    if (STREAM) return __ldcs(p);   // G larger than L2: evict-first
+    return __ldg(p);                // G L2-resident across iterations
+}
+
+// gate: skip when converged (GATE_RUNNING) or when no true residual is due
+// (GATE_TRUE); reduce: p^T w -> delta in the last block.
+template <typename T, bool STREAM>
+__global__ void __launch_bounds__(MV_THREADS)
+k_matvec_mat(const T* __restrict__ K, int64_t ldk, int64_t n, double lambda, int64_t chunk,
+             const double* __restrict__ pin, const double* __restrict__ z, double* __restrict__ pout,
+             int fuse, double* __restrict__ w, PcgScalars* sc, double* __restrict__ partials, int gate,
+             int reduce) {
+    if (gated_out(sc, gate)) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int64_t r1 = min(n, r0 + rows_per);
+    const int nrows = r1 > r0 ? (int)(r1 - r0) : 0;
+    T* ps = reinterpret_cast<T*>(smraw);
+    double* acc = reinterpret_cast<double*>(smraw + chunk * sizeof(T));
+    __shared__ double red[MV_THREADS / 32];
+    const double beta = fuse ? sc->beta : 0.0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) acc[i] = 0.0;
+
+    constexpr int VN = Vec16<T>::N;
+    using V = typename Vec16<T>::type;
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t clen = min(chunk, n - c0);
+        const int64_t cpad = (clen + VN - 1) / VN * VN;   // ldk padding is zero in G
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < cpad; j += blockDim.x) {
+            const int64_t gj = c0 + j;
+            double v = 0.0;
+            if (gj < n) v = fuse ? fma(beta, pin[gj], z[gj]) : pin[gj];
+            ps[j] = (T)v;
+        }
+        __syncthreads();
+        const int64_t nv = cpad / VN;
+        for (int rr = wid; rr < nrows; rr += nw) {
+            const V* row = reinterpret_cast<const V*>(K + (r0 + rr) * ldk + c0);
+            T s = T(0);
+            int64_t v = lane;
+            for (; v + 3 * 32 < nv; v += 4 * 32) {
+                const V a0 = ldk16<T, STREAM>(row + v), a1 = ldk16<T, STREAM>(row + v + 32);
+                const V a2 = ldk16<T, STREAM>(row + v + 64), a3 = ldk16<T, STREAM>(row + v + 96);
+                s += dot16<T>(a0, ps + v * VN) + dot16<T>(a1, ps + (v + 32) * VN) +
+                     dot16<T>(a2, ps + (v + 64) * VN) + dot16<T>(a3, ps + (v + 96) * VN);
+            }
+            for (; v < nv; v += 32) s += dot16<T>(ldk16<T, STREAM>(row + v), ps + v * VN);
+            s = lk::warp_sum(s);
+            if (lane == 0) acc[rr] += (double)s;
+        }
+    }
+    __syncthreads();
+    // epilogue: w = G p + lambda p, p^T w, and p_new for the owned rows
+    double pw = 0.0;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        const int64_t gi = r0 + i;
+        const double pi = fuse ? fma(beta, pin[gi], z[gi]) : pin[gi];
+        const double wi = fma(lambda, pi, acc[i]);
+        w[gi] = wi;
+        if (fuse) pout[gi] = pi;
+        pw = fma(pi, wi, pw);
+    }
+    if (sc == nullptr || !reduce) return;
+    pw = lk::block_sum(pw, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = pw;
+    if (lk::last_block(&sc->ticket[0])) {
+        const double pAp = lk::sum_partials(partials, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            sc->pAp = pAp;
+            if (!(pAp > 0.0) || !isfinite(pAp)) {
+                sc->converged = 2;
+                sc->delta = 0.0;
+            } else {
+                sc->delta = sc->rz / pAp;
+            }
+            sc->iters += 1;
+            sc->ticket[0] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Vector kernels.  Block b owns the contiguous rows [b*R, (b+1)*R).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void row_range(int64_t n, int64_t& r0, int64_t& r1) {
+    const int64_t R = (n + gridDim.x - 1) / gridDim.x;
+    r0 = min(n, (int64_t)blockIdx.x * R);
+    r1 = min(n, r0 + R);
+}
+
+// tpart[k] = sum_{i in [r0,r1)} U[i][k] * r[i]  for this block, fixed order.
+template <typename PT>
+__device__ void utr_partial(const PT* __restrict__ U, int n_r, int64_t r0, int64_t r1,
+                            const double* __restrict__ r, PT* __restrict__ tpart, PT* sm) {
+    const int G = (n_r >= (int)blockDim.x) ? 1 : (int)blockDim.x / n_r;
+    const int kth = (int)blockDim.x / G;
+    const int g = threadIdx.x / kth, kt = threadIdx.x % kth;
+    if (g < G) {
+        for (int k = kt; k < n_r; k += kth) {
+            PT a = PT(0);
+            for (int64_t i = r0 + g; i < r1; i += G) a += U[i * n_r + k] * (PT)r[i];
+            sm[g * n_r + k] = a;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_r; k += blockDim.x) {
+        PT a = PT(0);
+        for (int gg = 0; gg < G; ++gg) a += sm[gg * n_r + k];
+        tpart[k] = a;
+    }
+}
+
+template <typename PT>
+__device__ void reduce_t(const PT* __restrict__ tpart, int nb, int n_r, PT* __restrict__ t) {
+    for (int k = threadIdx.x; k < n_r; k += blockDim.x) {
+        PT a = PT(0);
+        for (int b = 0; b < nb; ++b) a += __ldcg(tpart + (int64_t)b * n_r + k);
+        t[k] = a;
+    }
+}
+
+struct PrecView {
+    int kind;
+    int n_r;
+    double cinv;
+    const void* U;
+    const void* W;
+    const double* dinv;
+};
+
+// INIT: alpha = 0, r = y, p = 0, |y|^2, t = U^T y.
+template <typename PT>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, double* __restrict__ r,
+           double* __restrict__ p0, PcgScalars* sc, double* __restrict__ partials, PrecView pv,
+           PT* __restrict__ tpart, PT* __restrict__ t, double tol) {
+    __shared__ double red[VEC_THREADS / 32];
+    __shared__ PT sm[1024];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    double yy = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double yi = y[i];
+        alpha[i] = 0.0;
+        r[i] = yi;
+        p0[i] = 0.0;
+        yy = fma(yi, yi, yy);
+    }
+    __syncthreads();
+    if (pv.kind == PRECOND_CCCP)
+        utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
+    yy = lk::block_sum(yy, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = yy;
+    if (lk::last_block(&sc->ticket[1])) {
+        const double tot = lk::sum_partials(partials, gridDim.x, red);
+        if (pv.kind == PRECOND_CCCP) reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
+        if (threadIdx.x == 0) {
+            sc->yy = tot;
+            sc->rr = tot;
+            sc->tol2yy = tol * tol * tot;
+            sc->rz = 0.0;
+            sc->beta = 0.0;
+            sc->delta = 0.0;
+            sc->iters = 0;
+            sc->true_count = 0;
+            sc->need_true = 0;
+            sc->converged = (tot == 0.0) ? 1 : (isfinite(tot) ? 0 : 2);
+            sc->ticket[1] = 0;
+        }
+    }
+}
+
+// UPD: alpha += delta p, r -= delta w, |r|^2, t = U^T r; stop / refinement decisions.
+template <typename PT>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__ w,
+             double* __restrict__ alpha, double* __restrict__ r, PcgScalars* sc,
+             double* __restrict__ partials, PrecView pv, PT* __restrict__ tpart, PT* __restrict__ t) {
+    if (gated_out(sc, GATE_RUNNING)) return;
+    __shared__ double red[VEC_THREADS / 32];
+    __shared__ PT sm[1024];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    const double delta = sc->delta;
+    double rr = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        alpha[i] = fma(delta, p[i], alpha[i]);
+        const double ri = fma(-delta, w[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+    }
+    __syncthreads();
+    if (pv.kind == PRECOND_CCCP)
+        utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
+    rr = lk::block_sum(rr, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = rr;
+    if (lk::last_block(&sc->ticket[2])) {
+        const double tot = lk::sum_partials(partials, gridDim.x, red);
+        if (pv.kind == PRECOND_CCCP) reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
+        if (threadIdx.x == 0) {
+            sc->rr = tot;
+            const int it = sc->iters;
+            const bool small = tot <= sc->tol2yy;
+            if (!isfinite(tot)) {
+                sc->converged = 2;
+            } else if (sc->refine_every == 0) {
+                if (small) sc->converged = 1;
+                else if (it >= sc->max_iter) sc->converged = 3;
+            } else {
+                if (small || (it % sc->refine_every) == 0 || it >= sc->max_iter) sc->need_true = 1;
+            }
+            sc->ticket[2] = 0;
+        }
+    }
+}
+
+// TR2: r = y - w2 with w2 = (lambda I + G64) alpha; stop test on the true residual.
+template <typename PT>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_true_residual(int64_t n, const double* __restrict__ y, const double* __restrict__ w2,
+                double* __restrict__ r, PcgScalars* sc, double* __restrict__ partials, PrecView pv,
+                PT* __restrict__ tpart, PT* __restrict__ t) {
+    if (gated_out(sc, GATE_TRUE)) return;
+    __shared__ double red[VEC_THREADS / 32];
+    __shared__ PT sm[1024];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    double rr = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double ri = y[i] - w2[i];
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+    }
+    __syncthreads();
+    if (pv.kind == PRECOND_CCCP)
+        utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
+    rr = lk::block_sum(rr, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = rr;
+    if (lk::last_block(&sc->ticket[3])) {
+        const double tot = lk::sum_partials(partials, gridDim.x, red);
+        if (pv.kind == PRECOND_CCCP) reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
+        if (threadIdx.x == 0) {
+            sc->rr = tot;
+            sc->rr_true = tot;
+            sc->true_count += 1;
+            sc->need_true = 0;
+            if (!isfinite(tot)) sc->converged = 2;
+            else if (tot <= sc->tol2yy) sc->converged = 1;
+            else if (sc->iters >= sc->max_iter) sc->converged = 3;
+            sc->ticket[3] = 0;
+        }
+    }
+}
+
+// PRE: z = P r, r^T z, beta.
+template <typename PT>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgScalars* sc,
+          double* __restrict__ partials, PrecView pv, const PT* __restrict__ t, int gate) {
+    if (gated_out(sc, gate)) return;
+    __shared__ double red[VEC_THREADS / 32];
+    __shared__ PT ts[1024];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    double rz = 0.0;
+    if (pv.kind == PRECOND_CCCP) {
+        for (int k = threadIdx.x; k < pv.n_r; k += blockDim.x) ts[k] = __ldcg(t + k);
+        __syncthreads();
+        const PT* W = (const PT*)pv.W;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int64_t i = r0 + wid; i < r1; i += nw) {
+            PT a = PT(0);
+            for (int k = lane; k < pv.n_r; k += 32) a += W[i * pv.n_r + k] * ts[k];
+            a = lk::warp_sum(a);
+            const double zi = fma(pv.cinv, r[i], (double)a);
+            if (lane == 0) {
+                z[i] = zi;
+                rz = fma(r[i], zi, rz);
+            }
+        }
+    } else {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const double ri = r[i];
+            const double zi = (pv.kind == PRECOND_JACOBI) ? ri * pv.dinv[i] : ri;
+            z[i] = zi;
+            rz = fma(ri, zi, rz);
+        }
+    }
+    if (sc == nullptr) return;
+    rz = lk::block_sum(rz, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = rz;
+    if (lk::last_block(&sc->ticket[4])) {
+        const double tot = lk::sum_partials(partials, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            const double old = sc->rz;
+            if (!isfinite(tot) || tot < 0.0) sc->converged = 2;
+            else if (tot == 0.0) sc->converged = 1;
+            sc->beta = (old > 0.0) ? tot / old : 0.0;
+            sc->rz = tot;
+            sc->ticket[4] = 0;
+        }
+    }
+}
+
+// |y - w|^2 -> sc->rr_true (final report only)
+__global__ void __launch_bounds__(VEC_THREADS)
+k_resid_norm(int64_t n, const double* __restrict__ y, const double* __restrict__ w, PcgScalars* sc,
+             double* __restrict__ partials) {
+    __shared__ double red[VEC_THREADS / 32];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double e = y[i] - w[i];
+        s = fma(e, e, s);
+    }
+    s = lk::block_sum(s, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (lk::last_block(&sc->ticket[5])) {
+        const double tot = lk::sum_partials(partials, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            sc->rr_true = tot;
+            sc->ticket[5] = 0;
+        }
+    }
+}
+
+// standalone U^T r  (preconditioner apply outside a solve)
+template <typename PT>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_utr(int64_t n, const double* __restrict__ r, PrecView pv, PT* __restrict__ tpart, PT* __restrict__ t,
+      unsigned int* ticket) {
+    __shared__ PT sm[1024];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
+    if (threadIdx.x == 0) { /* partial written by utr_partial */ }
+    if (lk::last_block(ticket)) {
+        reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
+        if (threadIdx.x == 0) *ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct Workspace {
+    double *r, *z, *p[2], *w, *w2, *partials;
+    void *tpart, *t;
+    PcgScalars* sc;
+    unsigned int* ticket;
+    int vec_blocks;
+    int mv_blocks;
+};
+
+int vec_blocks_for(const laker_ctx* ctx, int64_t n) {
+    int64_t b = (n + 63) / 64;
+    b = std::min<int64_t>(b, 2 * ctx->num_sms);
+    return (int)std::max<int64_t>(1, b);
+}
+int mv_blocks_for(const laker_ctx* ctx, int64_t n) {
+    int64_t b = std::min<int64_t>((n + 7) / 8, ctx->num_sms);
+    return (int)std::max<int64_t>(1, b);
+}
+
+constexpr size_t MV_SMEM_MAX = 200 * 1024;
+constexpr int64_t STREAM_BYTES = 48ll << 20;   // G above this size is streamed evict-first
+
+template <typename T>
+laker_status launch_mv(laker_ctx* ctx, const laker_op* op, const T* K, const double* pin, const double* z,
+                       double* pout, int fuse, double* w, PcgScalars* sc, double* partials, int gate,
+                       int reduce, int blocks) {
+    const int64_t n = op->n;
+    int64_t chunk = std::min<int64_t>((n + 3) / 4 * 4, (int64_t)(160 * 1024 / sizeof(T)));
+    chunk = chunk / 4 * 4;
+    const int64_t rows_per = (n + blocks - 1) / blocks;
+    const size_t smem = chunk * sizeof(T) + rows_per * sizeof(double);
+    if (smem > MV_SMEM_MAX) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "matvec row block too large");
+    const bool stream = (int64_t)(n * op->ldk * sizeof(T)) > STREAM_BYTES;
+    if (stream)
+        k_matvec_mat<T, true><<<blocks, MV_THREADS, smem, ctx->stream>>>(K, op->ldk, n, op->lambda, chunk, pin, z,
+                                                                        pout, fuse, w, sc, partials, gate, reduce);
+    else
+        k_matvec_mat<T, false><<<blocks, MV_THREADS, smem, ctx->stream>>>(K, op->ldk, n, op->lambda, chunk, pin, z,
+                                                                         pout, fuse, w, sc, partials, gate, reduce);
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}
+
+PrecView make_view(const laker_precond* P, bool use32) {
+    PrecView v{};
+    if (P == nullptr) { v.kind = PRECOND_IDENTITY; return v; }
+    v.kind = P->kind;
+    v.n_r = P->n_r;
+    v.cinv = P->cinvsqrt;
+    v.U = use32 ? (const void*)P->U32 : (const void*)P->U64;
+    v.W = use32 ? (const void*)P->W32 : (const void*)P->W64;
+    v.dinv = P->dinv;
+    return v;
+}
+
+laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws) {
+    const int64_t n = op->n;
+    ws.vec_blocks = vec_blocks_for(ctx, n);
+    ws.mv_blocks = mv_blocks_for(ctx, n);
+    laker_status st;
+    double* base = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&base, (size_t)6 * n * sizeof(double))) != LAKER_OK) return st;
+    ws.r = base; ws.z = base + n; ws.p[0] = base + 2 * n; ws.p[1] = base + 3 * n; ws.w = base + 4 * n;
+    ws.w2 = base + 5 * n;
+    const int nb = std::max(ws.vec_blocks, ws.mv_blocks) + 8;
+    if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
+    const int nr = std::max(1, n_r);
+    if ((st = lk_malloc(ctx, &ws.tpart, (size_t)ws.vec_blocks * nr * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, &ws.t, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&ws.sc, sizeof(PcgScalars))) != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMemsetAsync(ws.sc, 0, sizeof(PcgScalars), ctx->stream));
+    ws.ticket = ws.sc->ticket + 7;
+    return LAKER_OK;
+}
+void ws_free(Workspace& ws) {
+    cudaFree(ws.r);
+    cudaFree(ws.partials);
+    cudaFree(ws.tpart);
+    cudaFree(ws.t);
+    cudaFree(ws.sc);
+}
+
+template <typename PT>
+laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecView& pv, Workspace& ws,
+                               const double* y, double* alpha, int parity, bool mixed) {
+    const int64_t n = op->n;
+    double* pin = ws.p[parity];
+    double* pout = ws.p[parity ^ 1];
+    laker_status st;
+    // MV with the operator's inner precision
+    if (op->variant == LAKER_MATRIX_FREE) {
+        st = mf_matvec_launch(ctx, op, pin, ws.z, pout, ws.w, ws.sc, ws.partials, 1, nullptr, nullptr);
+    } else if (op->precision == LAKER_FP64) {
+        st = launch_mv<double>(ctx, op, op->K64, pin, ws.z, pout, 1, ws.w, ws.sc, ws.partials, GATE_RUNNING, 1,
+                               ws.mv_blocks);
+    } else {
+        st = launch_mv<float>(ctx, op, op->K32, pin, ws.z, pout, 1, ws.w, ws.sc, ws.partials, GATE_RUNNING, 1,
+                              ws.mv_blocks);
+    }
+    if (st != LAKER_OK) return st;
+    k_pcg_update<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, pout, ws.w, alpha, ws.r, ws.sc,
+                                                                      ws.partials, pv, (PT*)ws.tpart, (PT*)ws.t);
+    LK_LAUNCHED(ctx);
+    if (mixed) {
+        // TR1: w2 = (lambda I + G64) alpha, only when a true residual is due
+        if ((st = launch_mv<double>(ctx, op, op->K64, alpha, nullptr, nullptr, 0, ws.w2, ws.sc, nullptr,
+                                    GATE_TRUE, 0, ws.mv_blocks)) != LAKER_OK)
+            return st;
+        k_true_residual<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.r, ws.sc, ws.partials,
+                                                                             pv, (PT*)ws.tpart, (PT*)ws.t);
+        LK_LAUNCHED(ctx);
+    }
+    k_precond<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
+                                                                   (const PT*)ws.t, GATE_RUNNING);
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}
+
+}  // namespace
+
+laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
+    if (op->variant == LAKER_MATRIX_FREE)
+        return mf_matvec_launch(ctx, op, x, nullptr, nullptr, w, nullptr, nullptr, 0, nullptr, nullptr);
+    if (op->precision == LAKER_FP64)
+        return launch_mv<double>(ctx, op, op->K64, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
+                                 mv_blocks_for(ctx, op->n));
+    return launch_mv<float>(ctx, op, op->K32, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
+                            mv_blocks_for(ctx, op->n));
+}
+
+laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
+    return launch_mv<double>(ctx, op, op->K64, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
+                             mv_blocks_for(ctx, op->n));
+}
+
+laker_status pcg_prepare(laker_ctx* ctx) {
+    LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)MV_SMEM_MAX));
+    LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)MV_SMEM_MAX));
+    LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)MV_SMEM_MAX));
+    LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)MV_SMEM_MAX));
+    return LAKER_OK;
+}
+
+laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z) {
+    const int64_t n = P->n;
+    const int vb = vec_blocks_for(ctx, n);
+    PrecView pv = make_view(P, P->use32);
+    if (P->kind != PRECOND_CCCP) {
+        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, nullptr, GATE_NONE);
+        LK_LAUNCHED(ctx);
+        return LAKER_OK;
+    }
+    void *tpart = nullptr, *t = nullptr;
+    unsigned int* ticket = nullptr;
+    laker_status st;
+    if ((st = lk_malloc(ctx, &tpart, (size_t)vb * P->n_r * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, &t, (size_t)P->n_r * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&ticket, sizeof(unsigned int))) != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
+    if (P->use32) {
+        k_utr<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, pv, (float*)tpart, (float*)t, ticket);
+        LK_LAUNCHED(ctx);
+        k_precond<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, (const float*)t,
+                                                              GATE_NONE);
+    } else {
+        k_utr<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, pv, (double*)tpart, (double*)t, ticket);
+        LK_LAUNCHED(ctx);
+        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, (const double*)t,
+                                                               GATE_NONE);
+    }
+    LK_LAUNCHED(ctx);
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(tpart);
+    cudaFree(t);
+    cudaFree(ticket);
+    return LAKER_OK;
+}
+
+laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
+                       double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info) {
+    const int64_t n = op->n;
+    const bool mixed = (op->precision != LAKER_FP64) && refine_every > 0;
+    const bool use32 = (op->precision != LAKER_FP64);
+    Workspace ws{};
+    laker_status st = ws_alloc(ctx, op, P ? P->n_r : 0, ws);
+    if (st != LAKER_OK) return st;
+    PrecView pv = make_view(P, use32);
+    if (P && P->kind == PRECOND_CCCP && use32 && (P->U32 == nullptr || P->W32 == nullptr)) {
+        ws_free(ws);
+        return set_error(ctx, LAKER_ERR_ARG, "preconditioner has no float32 factors for this operator");
+    }
+    PcgScalars init{};
+    init.max_iter = max_iter;
+    init.refine_every = mixed ? refine_every : 0;
+    LK_CUDA(ctx, cudaMemcpyAsync(ws.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+
+    auto run_init = [&]() -> laker_status {
+        if (use32) {
+            k_pcg_init<float><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(
+                n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, pv, (float*)ws.tpart, (float*)ws.t, tol);
+            LK_LAUNCHED(ctx);
+            k_precond<float><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
+                                                                              (const float*)ws.t, GATE_RUNNING);
+        } else {
+            k_pcg_init<double><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(
+                n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, pv, (double*)ws.tpart, (double*)ws.t, tol);
+            LK_LAUNCHED(ctx);
+            k_precond<double><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
+                                                                               (const double*)ws.t, GATE_RUNNING);
+        }
+        LK_LAUNCHED(ctx);
+        return LAKER_OK;
+    };
+    if ((st = run_init()) != LAKER_OK) { ws_free(ws); return st; }
+
+    // capture a block of 2*H iterations (even/odd p buffers) into a graph
+    const int H = 8;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t launches_before = ctx->launches;
+    LK_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    for (int h = 0; h < H && st == LAKER_OK; ++h) {
+        for (int parity = 0; parity < 2 && st == LAKER_OK; ++parity) {
+            st = use32 ? enqueue_iteration<float>(ctx, op, pv, ws, y, alpha, parity, mixed)
+                       : enqueue_iteration<double>(ctx, op, pv, ws, y, alpha, parity, mixed);
+        }
+    }
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != LAKER_OK) { if (graph) cudaGraphDestroy(graph); ws_free(ws); return st; }
+    if (ce != cudaSuccess) { ws_free(ws); return set_error(ctx, LAKER_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce)); }
+    const int64_t per_replay = ctx->launches - launches_before;
+    ctx->launches = launches_before;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) { cudaGraphDestroy(graph); ws_free(ws); return set_error(ctx, LAKER_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
+
+    int* flag_host = nullptr;
+    LK_CUDA(ctx, cudaMallocHost(&flag_host, sizeof(int)));
+    const int max_replays = max_iter / (2 * H) + 2;
+    for (int rep = 0; rep < max_replays; ++rep) {
+        LK_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+        ctx->launches += per_replay;
+        LK_CUDA(ctx, cudaMemcpyAsync(flag_host, &ws.sc->converged, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (*flag_host != 0) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaFreeHost(flag_host);
+
+    // final report: float64-accurate residual of the returned alpha
+    if ((st = op_matvec_fp64(ctx, op, alpha, ws.w2)) != LAKER_OK) { ws_free(ws); return st; }
+    k_resid_norm<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.sc, ws.partials);
+    LK_LAUNCHED(ctx);
+    PcgScalars out{};
+    LK_CUDA(ctx, cudaMemcpyAsync(&out, ws.sc, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ws_free(ws);
+    laker_status result = LAKER_OK;
+    if (out.converged == 2) result = LAKER_ERR_BREAKDOWN;
+    else if (out.converged != 1) result = LAKER_ERR_MAXITER;
+    if (info) {
+        info->iterations = out.iters;
+        info->true_residuals = out.true_count;
+        info->converged = out.converged == 1;
+        info->rel_res = out.yy > 0 ? std::sqrt(out.rr / out.yy) : 0.0;
+        info->rel_res_true = out.yy > 0 ? std::sqrt(out.rr_true / out.yy) : 0.0;
+        info->status = result;
+    }
+    if (result != LAKER_OK)
+        return set_error(ctx, result, result == LAKER_ERR_BREAKDOWN ? "PCG breakdown" : "PCG reached max_iter");
+    return LAKER_OK;
+}

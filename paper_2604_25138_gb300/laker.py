@@ -1,0 +1,261 @@
+"""Thin Python binding of liblaker's C ABI (include/laker.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Device
+arrays are passed as torch CUDA tensors (float64, contiguous); torch is used
+for device memory and the current stream, nothing else.  If the shared library
+is missing this module raises on import of the library -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblaker.so")
+
+FP64, FP32, BF16X3 = 0, 1, 2
+AUTO, MATERIALISED, MATRIX_FREE = 0, 1, 2
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER = -1, -2, -3, -4, -5
+ERR_NONFINITE, ERR_TIMEOUT, ERR_OOM, ERR_UNSUPPORTED = -6, -7, -8, -9
+
+
+class LakerError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"laker status {status}: {msg}")
+        self.status = status
+
+
+class FitInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("c", ctypes.c_double),
+                ("rho", ctypes.c_double), ("change", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("true_residuals", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Load liblaker.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblaker.so not built ({LIB_PATH}); run paper_2604_25138_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    pvp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "laker_create": (i32, [pvp, i32, vp]),
+        "laker_destroy": (i32, [vp]),
+        "laker_last_error": (ctypes.c_char_p, [vp]),
+        "laker_status_string": (ctypes.c_char_p, [i32]),
+        "laker_launch_count": (i64, [vp]),
+        "laker_build_kernel": (i32, [vp, vp, i64, i32, f64, f64, i32, i32, pvp]),
+        "laker_op_destroy": (i32, [vp]),
+        "laker_op_matvec": (i32, [vp, vp, vp, vp]),
+        "laker_op_matvec_fp64": (i32, [vp, vp, vp, vp]),
+        "laker_fit_preconditioner": (i32, [vp, vp, vp, i32, f64, f64, f64, i32, f64, pvp,
+                                           ctypes.POINTER(FitInfo)]),
+        "laker_precond_jacobi": (i32, [vp, vp, pvp]),
+        "laker_precond_destroy": (i32, [vp]),
+        "laker_precond_apply": (i32, [vp, vp, vp, vp]),
+        "laker_precond_export": (i32, [vp, vp, vp, vp, vp]),
+        "laker_pcg_solve": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
+        "laker_eval_map": (i32, [vp, vp, vp, i64, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor | None, name: str, numel: int | None = None) -> int | None:
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return t.data_ptr()
+
+
+class Context:
+    """laker_create / laker_destroy; binds a device and the current torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        lib = library()
+        self.device = device
+        # The library captures PCG iterations into CUDA graphs, which needs a
+        # non-legacy stream; every call below orders this stream after the
+        # caller's current stream and the caller's stream after it.
+        with torch.cuda.device(device):
+            s = stream if stream is not None else torch.cuda.Stream(device)
+        self.stream = s
+        h = ctypes.c_void_p()
+        st = lib.laker_create(ctypes.byref(h), device, ctypes.c_void_p(s.cuda_stream))
+        if st != OK:
+            raise LakerError(st, "laker_create failed")
+        self.handle = h
+
+    def __enter__(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        return self
+
+    def __exit__(self, *exc):
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return False
+
+    def check(self, st: int, allowed=(OK,)):
+        if st not in allowed:
+            raise LakerError(st, library().laker_last_error(self.handle).decode())
+        return st
+
+    def launches(self) -> int:
+        return library().laker_launch_count(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().laker_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class Operator:
+    ctx: Context
+    handle: ctypes.c_void_p
+    n: int
+    d: int
+    precision: int
+    variant: int
+    Q: torch.Tensor
+
+    def close(self):
+        if self.handle:
+            library().laker_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class Preconditioner:
+    ctx: Context
+    handle: ctypes.c_void_p
+    n: int
+    n_r: int
+    info: dict
+
+    def close(self):
+        if self.handle:
+            library().laker_precond_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def laker_build_kernel(ctx: Context, Q: torch.Tensor, scale: float, lam: float, precision: int = FP64,
+                       variant: int = AUTO) -> Operator:
+    n, d = Q.shape
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_build_kernel(ctx.handle, _ptr(Q, "Q"), n, d, scale, lam, precision, variant,
+                                               ctypes.byref(h)))
+    return Operator(ctx, h, n, d, precision, variant, Q)
+
+
+def laker_op_matvec(ctx: Context, op: Operator, x: torch.Tensor, w: torch.Tensor | None = None,
+                    fp64: bool = False) -> torch.Tensor:
+    if w is None:
+        w = torch.empty_like(x)
+    fn = library().laker_op_matvec_fp64 if fp64 else library().laker_op_matvec
+    with ctx:
+        ctx.check(fn(ctx.handle, op.handle, _ptr(x, "x", op.n), _ptr(w, "w", op.n)))
+    return w
+
+
+def laker_fit_preconditioner(ctx: Context, op: Operator, Z: torch.Tensor, gamma: float = 0.1,
+                             rho: float = -1.0, eps: float = 1e-8, max_iter: int = 200,
+                             tol: float = 1e-10) -> Preconditioner:
+    n, n_r = Z.shape
+    info = FitInfo()
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_fit_preconditioner(ctx.handle, op.handle, _ptr(Z, "Z", op.n * n_r), n_r, gamma,
+                                                     rho, eps, max_iter, tol, ctypes.byref(h), ctypes.byref(info)))
+    d = {f: getattr(info, f) for f, _ in FitInfo._fields_}
+    return Preconditioner(ctx, h, n, n_r, d)
+
+
+def laker_precond_jacobi(ctx: Context, op: Operator) -> Preconditioner:
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_precond_jacobi(ctx.handle, op.handle, ctypes.byref(h)))
+    return Preconditioner(ctx, h, op.n, 0, {})
+
+
+def laker_precond_apply(ctx: Context, P: Preconditioner, r: torch.Tensor) -> torch.Tensor:
+    z = torch.empty_like(r)
+    with ctx:
+        ctx.check(library().laker_precond_apply(ctx.handle, P.handle, _ptr(r, "r", P.n), _ptr(z, "z", P.n)))
+    return z
+
+
+def laker_precond_export(ctx: Context, P: Preconditioner):
+    dev = torch.device("cuda", ctx.device)
+    c = torch.empty(1, dtype=torch.float64, device=dev)
+    D = torch.empty(P.n_r, dtype=torch.float64, device=dev)
+    U = torch.empty(P.n, P.n_r, dtype=torch.float64, device=dev)
+    with ctx:
+        ctx.check(library().laker_precond_export(ctx.handle, P.handle, c.data_ptr(), D.data_ptr(), U.data_ptr()))
+    return float(c.item()), D, U
+
+
+def laker_pcg_solve(ctx: Context, op: Operator, P: Preconditioner | None, y: torch.Tensor, tol: float,
+                    max_iter: int = 100000, refine_every: int = 0, alpha: torch.Tensor | None = None,
+                    allow_maxiter: bool = False):
+    if alpha is None:
+        alpha = torch.empty_like(y)
+    info = SolveInfo()
+    with ctx:
+        st = library().laker_pcg_solve(ctx.handle, op.handle, P.handle if P is not None else None,
+                                       _ptr(y, "y", op.n), _ptr(alpha, "alpha", op.n), tol, max_iter, refine_every,
+                                       ctypes.byref(info))
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    return alpha, {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+
+def laker_eval_map(ctx: Context, op: Operator, Qg: torch.Tensor, alpha: torch.Tensor,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+    m = Qg.shape[0]
+    if out is None:
+        out = torch.empty(m, dtype=torch.float64, device=alpha.device)
+    with ctx:
+        ctx.check(library().laker_eval_map(ctx.handle, op.handle, _ptr(Qg, "Qg", m * op.d), m,
+                                           _ptr(alpha, "alpha", op.n), _ptr(out, "out", m)))
+    return out
