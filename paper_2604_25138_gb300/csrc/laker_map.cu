@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "laker_device.cuh"
+#include "laker_df.cuh"
 
 namespace {
 
@@ -79,10 +80,120 @@ __global__ void k_sum_slices(int64_t m, int ns, const double* __restrict__ part,
     out[i] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float variant (float32 pipes): every kernel value exp(s <qg, q>) is
+// accurate to ~1e-14 relative.  The map sums alpha_i G(x, x_i) with |alpha| up to
+// ~|y| / lambda, so per-entry errors of float32 size (~1e-7) would reach tenths
+// of a dB; double-float keeps them far below 0.01 dB.
+// Thread = one query row (its embedding, pre-scaled by s, in registers);
+// block = 128 rows x one slice of training points staged 32 at a time.
+// ---------------------------------------------------------------------------
+constexpr int DF_ROWS = 128;
+constexpr int DF_TILE = 32;
+
+template <int DM>
+__global__ void __launch_bounds__(DF_ROWS)
+k_map_df(const float2* __restrict__ Qg_df, int64_t m, const float2* __restrict__ Q_df, int64_t n, int d,
+         const float2* __restrict__ alpha_df, int64_t tiles_per_slice, double* __restrict__ part) {
+    __shared__ float2 qs[DF_TILE][DM];
+    __shared__ float2 as[DF_TILE];
+    const int64_t row = (int64_t)blockIdx.x * DF_ROWS + threadIdx.x;
+    lk::df2 g[DM];
+#pragma unroll
+    for (int t = 0; t < DM; ++t) {
+        float2 v = make_float2(0.f, 0.f);
+        if (row < m && t < d) v = Qg_df[row * d + t];
+        g[t] = {v.x, v.y};
+    }
+    lk::df2 acc{0.f, 0.f};
+    const int64_t nt = (n + DF_TILE - 1) / DF_TILE;
+    const int64_t t0 = (int64_t)blockIdx.y * tiles_per_slice, t1 = min(nt, t0 + tiles_per_slice);
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t j0 = tile * DF_TILE;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < DF_TILE * DM; idx += DF_ROWS) {
+            const int r = idx / DM, t = idx % DM;
+            const int64_t j = j0 + r;
+            qs[r][t] = (j < n && t < d) ? Q_df[j * d + t] : make_float2(0.f, 0.f);
+        }
+        if (threadIdx.x < DF_TILE) {
+            const int64_t j = j0 + threadIdx.x;
+            as[threadIdx.x] = (j < n) ? alpha_df[j] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int jmax = (n - j0 < DF_TILE) ? (int)(n - j0) : DF_TILE;
+        for (int r = 0; r < jmax; ++r) {
+            lk::Dot2 dot;
+#pragma unroll
+            for (int t = 0; t < DM; ++t) {
+                if (t < d) {
+                    const float2 q = qs[r][t];
+                    dot.add(g[t], lk::df2{q.x, q.y});
+                }
+            }
+            const lk::df2 e = lk::df_exp(dot.value());
+            const float2 a = as[r];
+            acc = lk::df_add(acc, lk::df_mul(e, lk::df2{a.x, a.y}));
+        }
+    }
+    if (row < m) part[(int64_t)blockIdx.y * m + row] = lk::df_to(acc);
+}
+
+// x (float64, count) -> double-float pairs of scale * x
+__global__ void k_to_df(int64_t count, const double* __restrict__ x, double scale, float2* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const lk::df2 v = lk::df_from(x[i] * scale);
+    y[i] = make_float2(v.hi, v.lo);
+}
+
 }  // namespace
+
+static laker_status eval_map_df(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
+                                double* out) {
+    static int table_ready_dev = -1;
+    if (table_ready_dev != ctx->device) {
+        LK_CUDA(ctx, lk::df_exp_init());
+        table_ready_dev = ctx->device;
+    }
+    const int64_t n = op->n;
+    const int d = op->d;
+    float2 *qg = nullptr, *q = nullptr, *a = nullptr;
+    double* part = nullptr;
+    laker_status st;
+    if ((st = lk_malloc(ctx, (void**)&qg, (size_t)m * d * sizeof(float2))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&q, (size_t)n * d * sizeof(float2))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&a, (size_t)n * sizeof(float2))) != LAKER_OK) return st;
+    k_to_df<<<(unsigned)((m * d + 255) / 256), 256, 0, ctx->stream>>>(m * d, Qg, op->scale, qg);
+    LK_LAUNCHED(ctx);
+    k_to_df<<<(unsigned)((n * d + 255) / 256), 256, 0, ctx->stream>>>(n * d, op->Q64, 1.0, q);
+    LK_LAUNCHED(ctx);
+    k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, alpha, 1.0, a);
+    LK_LAUNCHED(ctx);
+    const int64_t mt = (m + DF_ROWS - 1) / DF_ROWS, nt = (n + DF_TILE - 1) / DF_TILE;
+    int64_t slices = std::max<int64_t>(1, std::min<int64_t>(nt, (4 * ctx->num_sms + mt - 1) / mt));
+    const int64_t per = (nt + slices - 1) / slices;
+    slices = (nt + per - 1) / per;
+    if ((st = lk_malloc(ctx, (void**)&part, (size_t)slices * m * sizeof(double))) != LAKER_OK) return st;
+    dim3 grid((unsigned)mt, (unsigned)slices);
+    if (d <= 16) k_map_df<16><<<grid, DF_ROWS, 0, ctx->stream>>>(qg, m, q, n, d, a, per, part);
+    else if (d <= 32) k_map_df<32><<<grid, DF_ROWS, 0, ctx->stream>>>(qg, m, q, n, d, a, per, part);
+    else if (d <= 64) k_map_df<64><<<grid, DF_ROWS, 0, ctx->stream>>>(qg, m, q, n, d, a, per, part);
+    else return set_error(ctx, LAKER_ERR_UNSUPPORTED, "double-float map supports d <= 64");
+    LK_LAUNCHED(ctx);
+    k_sum_slices<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(m, (int)slices, part, out);
+    LK_LAUNCHED(ctx);
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(qg);
+    cudaFree(q);
+    cudaFree(a);
+    cudaFree(part);
+    return LAKER_OK;
+}
 
 laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
                       double* out) {
+    if (op->precision != LAKER_FP64) return eval_map_df(ctx, op, Qg, m, alpha, out);
     const int64_t n = op->n;
     const int64_t mt = (m + BT - 1) / BT, nt = (n + BT - 1) / BT;
     int64_t slices = std::max<int64_t>(1, std::min<int64_t>(nt, (2 * ctx->num_sms + mt - 1) / mt));

@@ -237,3 +237,22 @@ def test_fp32_mixed_refinement_reaches_true_tolerance(L, ctx):
     a_star = O.solve_direct(A, inst.y)
     kappa_bound = 1.0 + n * np.mean(O.kernel_matrix(inst.Q, inst.scale)) / inst.lam
     assert rel(a, a_star) <= kappa_bound * 1e-6
+
+
+@pytest.mark.parametrize("n,d,m", [(1000, 16, 333), (2048, 32, 4096), (777, 64, 1025)])
+def test_map_double_float_matches_oracle(L, ctx, n, d, m):
+    """Mixed operators evaluate the radio map in double-float arithmetic on the
+    float32 pipes.  With |alpha| ~ |y| / lambda the map needs ~1e-10 relative
+    accuracy per kernel value to stay well under 0.01 dB; checked against the
+    float64 oracle map of the same alpha."""
+    from tests.gpu_util import dev, host, rel
+    inst = _inst(n, d, 1e-4, 40 + d, grid=int(math.ceil(math.sqrt(m))))
+    Qg = inst.Qg[:m]
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    alpha = O.solve_direct(A, inst.y)           # large, oscillating coefficients
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP32)
+    f = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha)))
+    fref = O.radio_map(Qg, inst.Q, alpha, inst.scale)
+    db = inst.y_sigma * (f - fref)
+    assert math.sqrt(np.mean(db ** 2)) < 1e-4
+    assert rel(f, fref) < 1e-8
