@@ -170,6 +170,23 @@ laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_pre
 laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
                             const double* alpha, double* out);
 
+/*
+ * Radio map without device allocation (no counterpart in the paper; a
+ * deployment variant of laker_eval_map with the same arguments and results).
+ * For callers that cannot call cudaMalloc -- services whose device memory is
+ * owned and pre-reserved by another allocator, or loops that must not
+ * synchronise the device, as cudaMalloc and cudaFree do.  Scratch comes from a
+ * static 32 MiB device array that every GPU loading this library keeps until
+ * exit; its address is looked up on the first call per device (make that call
+ * before any stream capture).  The call is asynchronous on the context's
+ * stream.  All calls on a device share the array: calls that overlap on the
+ * GPU race, so serialise them.
+ * Errors: LAKER_ERR_ARG if the scratch needed, (m d + n d + n) * 8 bytes for
+ * FP32/BF16X3 operators plus 8 m bytes of partial sums, exceeds 32 MiB.
+ */
+laker_status laker_eval_map_noalloc(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                                    const double* alpha, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -211,3 +211,108 @@ laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int6
     cudaFree(part);
     return LAKER_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Radio map without device allocation.
+//
+// Some callers cannot call cudaMalloc: services whose device memory is owned
+// and fully pre-reserved by another allocator (a framework's caching
+// allocator, a fixed-budget real-time process), or loops that must not
+// synchronise the device, which cudaMalloc and cudaFree do.  This variant
+// launches the same map kernels as laker_eval_map but takes its scratch (the
+// double-float copies of the inputs and the per-slice partial sums) from the
+// static device array below instead of allocating it.
+//
+// * The array is LAKER_MAP_SCRATCH_BYTES (32 MiB) per device, resident on every
+//   GPU that loads this library until the process exits.
+// * Host code cannot use the array's name as a device address; its address is
+//   looked up once per device with cudaGetSymbolAddress, with that device
+//   current, on the first call for that device.  Make that first call before
+//   any stream capture.
+// * Every call on a device shares the array and leaves its contents behind.
+//   Each kernel writes every scratch element it later reads, so nothing has
+//   to start at zero.  Calls whose work overlaps on the GPU (other streams,
+//   other threads) race on the array: serialise them.
+// ---------------------------------------------------------------------------
+#define LAKER_MAP_SCRATCH_BYTES (32u << 20)
+
+static __device__ __align__(256) unsigned char g_map_scratch[LAKER_MAP_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+bool g_table_ready[kMaxDevices] = {false};
+}  // namespace
+
+static laker_status noalloc_setup(laker_ctx* ctx, void** scratch) {
+    if (ctx->device < 0 || ctx->device >= kMaxDevices)
+        return set_error(ctx, LAKER_ERR_ARG, "device index out of range for the static scratch table");
+    if (g_scratch_ptr[ctx->device] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_map_scratch);
+        if (e != cudaSuccess)
+            return set_error(ctx, LAKER_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_scratch_ptr[ctx->device] = p;
+    }
+    if (!g_table_ready[ctx->device]) {
+        LK_CUDA(ctx, lk::df_exp_init());
+        g_table_ready[ctx->device] = true;
+    }
+    *scratch = g_scratch_ptr[ctx->device];
+    return LAKER_OK;
+}
+
+extern "C" laker_status laker_eval_map_noalloc(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                                               const double* alpha, double* out) {
+    if (!ctx) return LAKER_ERR_ARG;
+    if (!op || !Qg || !alpha || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (m < 1) return set_error(ctx, LAKER_ERR_ARG, "need m >= 1");
+    LK_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = op->n;
+    const int d = op->d;
+    const bool df = op->precision != LAKER_FP64;
+    if (df && d > 64) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "double-float map supports d <= 64");
+    // fixed part of the scratch: double-float copies of Qg, Q and alpha
+    const size_t fixed = df ? ((size_t)m * d + (size_t)n * d + (size_t)n) * sizeof(float2) : 0;
+    const size_t fixed_al = (fixed + 255) / 256 * 256;
+    if (fixed_al + (size_t)m * sizeof(double) > LAKER_MAP_SCRATCH_BYTES)
+        return set_error(ctx, LAKER_ERR_ARG,
+                         "laker_eval_map_noalloc: " + std::to_string(fixed_al + (size_t)m * sizeof(double)) +
+                             " bytes of scratch needed, the static scratch holds " +
+                             std::to_string(LAKER_MAP_SCRATCH_BYTES) + "; use laker_eval_map");
+    void* base = nullptr;
+    laker_status st = noalloc_setup(ctx, &base);
+    if (st != LAKER_OK) return st;
+    unsigned char* sb = static_cast<unsigned char*>(base);
+    const int64_t rows = df ? DF_ROWS : BT;
+    const int64_t tile = df ? DF_TILE : BT;
+    const int64_t mt = (m + rows - 1) / rows, nt = (n + tile - 1) / tile;
+    const int64_t want = df ? 4 * ctx->num_sms : 2 * ctx->num_sms;
+    int64_t slices = std::max<int64_t>(1, std::min<int64_t>(nt, (want + mt - 1) / mt));
+    const int64_t fit = (int64_t)((LAKER_MAP_SCRATCH_BYTES - fixed_al) / ((size_t)m * sizeof(double)));
+    slices = std::min(slices, fit);
+    const int64_t per = (nt + slices - 1) / slices;
+    slices = (nt + per - 1) / per;
+    double* part = reinterpret_cast<double*>(sb + fixed_al);
+    dim3 grid((unsigned)mt, (unsigned)slices);
+    if (df) {
+        float2* qg = reinterpret_cast<float2*>(sb);
+        float2* q = qg + (size_t)m * d;
+        float2* a = q + (size_t)n * d;
+        k_to_df<<<(unsigned)((m * d + 255) / 256), 256, 0, ctx->stream>>>(m * d, Qg, op->scale, qg);
+        LK_LAUNCHED(ctx);
+        k_to_df<<<(unsigned)((n * d + 255) / 256), 256, 0, ctx->stream>>>(n * d, op->Q64, 1.0, q);
+        LK_LAUNCHED(ctx);
+        k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, alpha, 1.0, a);
+        LK_LAUNCHED(ctx);
+        if (d <= 16) k_map_df<16><<<grid, DF_ROWS, 0, ctx->stream>>>(qg, m, q, n, d, a, per, part);
+        else if (d <= 32) k_map_df<32><<<grid, DF_ROWS, 0, ctx->stream>>>(qg, m, q, n, d, a, per, part);
+        else k_map_df<64><<<grid, DF_ROWS, 0, ctx->stream>>>(qg, m, q, n, d, a, per, part);
+    } else {
+        k_map_fp64<<<grid, 256, 0, ctx->stream>>>(Qg, m, op->Q64, n, d, op->scale, alpha, per, part);
+    }
+    LK_LAUNCHED(ctx);
+    k_sum_slices<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(m, (int)slices, part, out);
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}

@@ -72,6 +72,7 @@ def library() -> ctypes.CDLL:
         "laker_precond_export": (i32, [vp, vp, vp, vp, vp]),
         "laker_pcg_solve": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
         "laker_eval_map": (i32, [vp, vp, vp, i64, vp, vp]),
+        "laker_eval_map_noalloc": (i32, [vp, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,4 +259,16 @@ def laker_eval_map(ctx: Context, op: Operator, Qg: torch.Tensor, alpha: torch.Te
     with ctx:
         ctx.check(library().laker_eval_map(ctx.handle, op.handle, _ptr(Qg, "Qg", m * op.d), m,
                                            _ptr(alpha, "alpha", op.n), _ptr(out, "out", m)))
+    return out
+
+
+def laker_eval_map_noalloc(ctx: Context, op: Operator, Qg: torch.Tensor, alpha: torch.Tensor,
+                           out: torch.Tensor) -> torch.Tensor:
+    """Radio map for callers that cannot allocate device memory: the library
+    takes its scratch from a static device array (see include/laker.h) and
+    `out` must be supplied by the caller."""
+    m = Qg.shape[0]
+    with ctx:
+        ctx.check(library().laker_eval_map_noalloc(ctx.handle, op.handle, _ptr(Qg, "Qg", m * op.d), m,
+                                                   _ptr(alpha, "alpha", op.n), _ptr(out, "out", m)))
     return out
