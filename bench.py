@@ -57,6 +57,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def peaks_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["bf16_tflops"], "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -149,7 +158,7 @@ def run_ours(args):
         op.close()
         return alpha, fmap, info, P.info
 
-    mixed = dict(precision=L.FP32, refine=c["refine_every"])
+    mixed = dict(precision=L.BF16X3, refine=c["refine_every"])
     for _ in range(args.warmup):
         step(Q, y, Z, Qg, **mixed)
     torch.cuda.synchronize()
@@ -196,27 +205,29 @@ def run_ours(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    # roofline of the dominant kernel: the streamed float32 matvec of G
-    op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32)
+    # roofline of the dominant kernel: the tcgen05 matrix-free operator.  Per pair
+    # it executes 4 split-bf16 products of 2 * dpad flops on the tensor pipe and
+    # one ex2 on the MUFU pipe; the binding roof is the larger of the two times.
+    op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.BF16X3)
     x = to_dev(synth.random_vector(inst.n, 1))
-    w = torch.empty_like(x)
-    for _ in range(3):
-        L.laker_op_matvec(ctx, op, x, w)
-    reps = 30
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(ctx.stream)
-    for _ in range(reps):
-        L.laker_op_matvec(ctx, op, x, w)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    mv_ms = e0.elapsed_time(e1) / reps
-    n = inst.n
-    ldk = (n + 3) // 4 * 4
-    mv_bytes = n * ldk * 4 + 3 * n * 8
-    peak, peak_kind = peaks()
-    achieved = mv_bytes / (mv_ms * 1e-3) / 1e9
+    mv_ms = L.laker_op_time_operator(ctx, op, x, reps=30)
     op.close()
+    n = inst.n
+    dpad = (inst.d + 15) // 16 * 16
+    pairs = float(n) * n
+    flops = pairs * 4 * 2 * dpad
+    bf16_peak, peak_kind = peaks_bf16()
+    sfu_peak = 32 * 152 * 2.07e9                     # ex2/s: 32 per clock per SM (measured) x SMs x max clock
+    t_tensor = flops / (bf16_peak * 1e12)
+    t_sfu = pairs / sfu_peak
+    achieved = flops / (mv_ms * 1e-3) / 1e12
+    # the streamed float32 materialised matvec, for the variant comparison
+    opm = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32)
+    mat_ms = L.laker_op_time_operator(ctx, opm, x, reps=30)
+    opm.close()
+    ldk = (n + 3) // 4 * 4
+    mat_gbs = (n * ldk * 4 + 3 * n * 8) / (mat_ms * 1e-3) / 1e9
+    hbm, hbm_kind = peaks()
 
     # plain float64 path on the same instance (the paper's method in float64)
     plain = None
@@ -241,22 +252,26 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x4+f32+f64", "data": "synthetic",
         "config": {"workload": "single instance, n=16384 clustered, d=32, lambda=1e-4, 8 Tx, 512x512 grid, "
                                "N_r=%d, tol 1e-6 true residual" % n_r,
                    "n": n, "d": inst.d, "lambda": inst.lam, "n_r": n_r, "grid": CFG["grid"] ** 2,
-                   "operator": "materialised float32 G, float64 residual every 20 products",
-                   "l2": "inputs larger than L2 (G is 1 GiB float32 + 2 GiB float64)",
+                   "operator": "matrix-free tcgen05 split-bf16 logits + ex2, double-float residual every 20 products",
+                   "l2": "working set larger than L2 (G kept as a 2 GiB float32 pair for true residuals)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "solve": {"iterations": info["iterations"], "true_residuals": info["true_residuals"],
                   "rel_res_true": info["rel_res_true"], "cccp_iterations": finfo["iterations"]},
         "plain_fp64": plain,
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_matvec_mat<float> (streamed G, fused PCG epilogue)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "bytes_per_launch": mv_bytes,
-                     "ms_per_launch": mv_ms},
+        "roofline": {"kernel": "k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, row sums)", "bound": "tensor",
+                     "achieved": achieved, "peak": bf16_peak, "peak_kind": peak_kind + " bf16 burst",
+                     "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                     "flops_per_launch": flops, "ms_per_launch": mv_ms,
+                     "tensor_bound_ms": t_tensor * 1e3, "sfu_bound_ms": t_sfu * 1e3,
+                     "frac_of_binding_roof": max(t_tensor, t_sfu) * 1e3 / mv_ms},
+        "materialised_fp32_matvec": {"ms_per_launch": mat_ms, "achieved_gbs": mat_gbs, "peak_gbs": hbm,
+                                     "frac": mat_gbs / hbm},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

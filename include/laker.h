@@ -46,7 +46,8 @@ typedef enum {
 typedef enum {
     LAKER_FP64 = 0,      /* float64 logits, exp and accumulation */
     LAKER_FP32 = 1,      /* float32 storage / arithmetic, float64 PCG scalars */
-    LAKER_BF16X3 = 2     /* split-bf16 logits on tensor cores, float32 exp and sums */
+    LAKER_BF16X3 = 2     /* split-bf16 logits (q = hi + lo, all hi/lo products) on tensor
+                            cores, float32 exp2 and sums; matrix-free */
 } laker_precision;
 
 /* How the operator v -> (lambda I + G) v is evaluated. */
@@ -98,8 +99,9 @@ int64_t laker_launch_count(const laker_ctx* ctx);
  *   scale   1.0 reproduces the paper's exp(<e_i,e_j>); 1/sqrt(d) gives the
  *           scaled dot-product form.
  *   lambda  ridge parameter, must be > 0.
- *   precision / variant  see the enums.  FP32 and BF16X3 operators also keep a
- *           float64-accurate materialised G for true-residual recomputation.
+ *   precision / variant  see the enums.  FP32 and BF16X3 operators keep G as a
+ *           float32 pair (hi, lo) with hi + lo equal to G to ~2^-48: hi is the
+ *           float32 operator, hi + lo gives float64-accurate true residuals.
  * Errors: LAKER_ERR_ARG for n < 1, d < 1 or d > 256, lambda <= 0;
  *         LAKER_ERR_OOM if G does not fit.
  */
@@ -112,6 +114,15 @@ laker_status laker_op_destroy(laker_op* op);
 laker_status laker_op_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
 /* w = (lambda I + G) x with the float64-accurate operator. */
 laker_status laker_op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
+
+/*
+ * Measurement hook (no counterpart in the paper): average device time in
+ * milliseconds of the operator's main kernel alone -- the streamed matvec of a
+ * materialised operator, the tensor-core kernel of a matrix-free one -- over
+ * `reps` back-to-back launches on x (device, n), timed with CUDA events on the
+ * context's stream after one warm-up launch.  Used for roofline reporting.
+ */
+laker_status laker_op_time_operator(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 
 /*
  * Preconditioner learning (Algorithm 1, learning stage; Sec. IV-B Eq.

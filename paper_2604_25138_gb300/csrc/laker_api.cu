@@ -36,12 +36,14 @@ laker_status check_ctx(laker_ctx* ctx) {
 
 void free_op(laker_op* op) {
     if (!op) return;
+    mf_release(op);
     cudaFree(op->Q64);
     cudaFree(op->Qhi);
     cudaFree(op->Qlo);
     cudaFree(op->Q32);
     cudaFree(op->K64);
     cudaFree(op->K32);
+    cudaFree(op->K32lo);
     cudaFree(op->diagA);
     delete op;
 }
@@ -191,6 +193,14 @@ laker_status laker_op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const doub
     if (st != LAKER_OK) return st;
     if (!op || !x || !w) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
     return op_matvec_fp64(ctx, op, x, w);
+}
+
+laker_status laker_op_time_operator(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !x || !ms || reps < 1) return set_error(ctx, LAKER_ERR_ARG, "bad arguments");
+    if (op->variant == LAKER_MATRIX_FREE) return mf_time_main(ctx, op, x, reps, ms);
+    return op_time_materialised(ctx, op, x, reps, ms);
 }
 
 laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma,

@@ -4,7 +4,10 @@
 // G is symmetric, so only tiles (bi <= bj) are evaluated and each off-diagonal
 // tile is written twice (direct and, through a shared-memory transpose,
 // mirrored), halving the float64 exponentials -- the dominant cost on GB300,
-// whose float64 pipe runs at ~1/74 of the float32 rate.
+// whose float64 pipe runs at ~1/74 of the float32 rate.  Float64 operators
+// store G in float64; mixed operators store the float32 pair (hi, lo) with
+// hi = fl32(G), lo = fl32(G - hi): hi alone is the float32 operator, hi + lo is
+// G to ~2^-48 for the double-float true residual, in the same 8 bytes/entry.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -16,10 +19,10 @@ namespace {
 constexpr int BT = 64;   // output tile edge
 constexpr int BD = 32;   // embedding-dimension chunk
 
-template <bool W32>
+template <bool PAIR>
 __global__ void __launch_bounds__(256)
 k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
-            double* __restrict__ K64, float* __restrict__ K32, int64_t ldk, int nt) {
+            double* __restrict__ K64, float* __restrict__ K32, float* __restrict__ K32lo, int64_t ldk, int nt) {
     // blockIdx.x enumerates the upper-triangular tile pairs row by row.
     int64_t t = blockIdx.x;
     int bi = 0;
@@ -72,8 +75,13 @@ k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
             const double g = exp(scale * acc[u][v]);
             T[r][c] = g;
             if (i < n && j < n) {
-                K64[i * ldk + j] = g;
-                if (W32) K32[i * ldk + j] = (float)g;
+                if (PAIR) {
+                    const float h = (float)g;
+                    K32[i * ldk + j] = h;
+                    K32lo[i * ldk + j] = (float)(g - (double)h);
+                } else {
+                    K64[i * ldk + j] = g;
+                }
             }
         }
     }
@@ -84,8 +92,13 @@ k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
         const int64_t oi = (int64_t)bj * BT + c, oj = (int64_t)bi * BT + r;
         if (oi < n && oj < n) {
             const double g = T[r][c];
-            K64[oi * ldk + oj] = g;
-            if (W32) K32[oi * ldk + oj] = (float)g;
+            if (PAIR) {
+                const float h = (float)g;
+                K32[oi * ldk + oj] = h;
+                K32lo[oi * ldk + oj] = (float)(g - (double)h);
+            } else {
+                K64[oi * ldk + oj] = g;
+            }
         }
     }
 }
@@ -124,29 +137,33 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
     const int d = op->d;
     op->ldk = (n + 3) / 4 * 4;
     op->dpad = (d + 15) / 16 * 16;
-    // float32 copy of G: the materialised FP32 operator, and the float32 GEMM of
-    // the preconditioner fit for every non-FP64 operator
-    const bool need32 = (op->precision != LAKER_FP64);
-    const size_t kbytes64 = (size_t)n * op->ldk * sizeof(double);
+    const bool pair = (op->precision != LAKER_FP64);
     laker_status st;
-    if ((st = lk_malloc(ctx, (void**)&op->K64, kbytes64)) != LAKER_OK) return st;
-    if (need32 && (st = lk_malloc(ctx, (void**)&op->K32, (size_t)n * op->ldk * sizeof(float))) != LAKER_OK)
-        return st;
+    if (pair) {
+        if ((st = lk_malloc(ctx, (void**)&op->K32, (size_t)n * op->ldk * sizeof(float))) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&op->K32lo, (size_t)n * op->ldk * sizeof(float))) != LAKER_OK) return st;
+    } else {
+        if ((st = lk_malloc(ctx, (void**)&op->K64, (size_t)n * op->ldk * sizeof(double))) != LAKER_OK) return st;
+    }
     if ((st = lk_malloc(ctx, (void**)&op->diagA, (size_t)n * sizeof(double))) != LAKER_OK) return st;
     if (op->ldk > n) {
-        LK_CUDA(ctx, cudaMemset2DAsync(op->K64 + n, op->ldk * sizeof(double), 0,
-                                       (op->ldk - n) * sizeof(double), n, ctx->stream));
-        if (need32)
-            LK_CUDA(ctx, cudaMemset2DAsync(op->K32 + n, op->ldk * sizeof(float), 0,
-                                           (op->ldk - n) * sizeof(float), n, ctx->stream));
+        if (pair) {
+            LK_CUDA(ctx, cudaMemset2DAsync(op->K32 + n, op->ldk * sizeof(float), 0, (op->ldk - n) * sizeof(float), n,
+                                           ctx->stream));
+            LK_CUDA(ctx, cudaMemset2DAsync(op->K32lo + n, op->ldk * sizeof(float), 0, (op->ldk - n) * sizeof(float),
+                                           n, ctx->stream));
+        } else {
+            LK_CUDA(ctx, cudaMemset2DAsync(op->K64 + n, op->ldk * sizeof(double), 0, (op->ldk - n) * sizeof(double), n,
+                                           ctx->stream));
+        }
     }
     const int nt = (int)((n + BT - 1) / BT);
     const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
-    if (need32)
-        k_build_sym<true><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64,
-                                                                    op->K32, op->ldk, nt);
+    if (pair)
+        k_build_sym<true><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, op->K32,
+                                                                    op->K32lo, op->ldk, nt);
     else
-        k_build_sym<false><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64,
+        k_build_sym<false><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64, nullptr,
                                                                      nullptr, op->ldk, nt);
     LK_LAUNCHED(ctx);
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->lambda,
@@ -163,6 +180,7 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
         k_split_bf16<<<(unsigned)((e + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->dpad, fold,
                                                                            op->Qhi, op->Qlo, op->Q32);
         LK_LAUNCHED(ctx);
+        if ((st = mf_prepare(ctx, op)) != LAKER_OK) return st;
     }
     return LAKER_OK;
 }

@@ -87,6 +87,35 @@ struct Dot2 {
     }
 };
 
+// Dot product with the compensation itself accumulated error-free (the K = 3
+// case of Ogita, Rump and Oishi's DotK): value = p + s + c.  Needed when the
+// terms are orders of magnitude larger than the result -- e.g. (lambda I + G)
+// alpha near convergence, |G_ij alpha_j| ~ 1e4 against an O(1) sum -- where
+// Dot2's float32 compensation term would leave ~1e-7 absolute noise.
+struct Dot3 {
+    float p = 0.f, s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(df2 a, df2 b) {
+        float h, r, q, np, ns, e;
+        two_prod(a.hi, b.hi, h, r);
+        two_sum(p, h, np, q);
+        p = np;
+        float t = __fadd_rn(q, r);
+        t = __fmaf_rn(a.hi, b.lo, t);
+        t = __fmaf_rn(a.lo, b.hi, t);
+        two_sum(s, t, ns, e);
+        s = ns;
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ df2 value() const {
+        df2 r;
+        two_sum(p, s, r.hi, r.lo);
+        r.lo = __fadd_rn(r.lo, c);
+        df2 o;
+        fast_two_sum(r.hi, r.lo, o.hi, o.lo);
+        return o;
+    }
+};
+
 // 2^(j/64), j = 0..63, as double-float pairs.  Constant memory is per
 // translation unit: every unit that calls df_exp calls df_exp_init() on the
 // host before its first launch.

@@ -52,9 +52,11 @@ struct laker_op {
     uint16_t* Qhi = nullptr;  // n x dpad bf16, high part of Q * sqrt(scale * log2 e)
     uint16_t* Qlo = nullptr;  // n x dpad bf16, low part
     float* Q32 = nullptr;     // n x d float copy
-    double* K64 = nullptr;    // n x ldk, G in float64
-    float* K32 = nullptr;     // n x ldk, G rounded to float
+    double* K64 = nullptr;    // n x ldk, G in float64 (float64 operators)
+    float* K32 = nullptr;     // n x ldk, G rounded to float (mixed operators)
+    float* K32lo = nullptr;   // n x ldk, G - K32 rounded to float: K32 + K32lo is G to ~2^-48
     double* diagA = nullptr;  // n, lambda + G_ii
+    void* mf = nullptr;       // matrix-free operator workspace (tensor maps, buffers)
 };
 
 enum PrecondKind { PRECOND_IDENTITY = 0, PRECOND_JACOBI = 1, PRECOND_CCCP = 2 };
@@ -113,6 +115,11 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
 laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
                       const double* alpha, double* out);
 // laker_mf.cu (matrix-free operator)
+laker_status mf_prepare(laker_ctx* ctx, laker_op* op);
+void mf_release(laker_op* op);
+laker_status mf_status(laker_ctx* ctx, const laker_op* op);
+laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status mf_matvec_launch(laker_ctx* ctx, const laker_op* op, const double* pin,
                               const double* z, double* pout, double* w, PcgScalars* sc,
                               double* partials, int fuse_p, float* pbuf, float* wbuf);

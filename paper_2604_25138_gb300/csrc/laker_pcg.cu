@@ -9,8 +9,14 @@
 //   UPD  alpha += delta p, r -= delta w, |r|^2, U^T r partials
 //        -> last block: stop test, t = U^T r
 //   [TR1, TR2]  only when a float64-accurate residual is due (mixed forms):
-//        w2 = (lambda I + G64) alpha, r = y - w2, stop test on the true residual
+//        w2 = (lambda I + G) alpha in compensated double-float, r = y - w2
+//        replaces the recursive residual (reliable updates), stop test on |r|
 //   PRE  z = P r, r^T z -> last block: beta = r.z_new / r.z_old
+//
+// The replaced residual must be accurate well below the tolerance: near
+// convergence |G_ij alpha_j| ~ 1e4 terms cancel to O(1) sums, and a residual
+// with ~1e-7 noise (plain double-float Dot2) was observed to make the
+// replacements diverge at kappa ~ 1e8; the Dot3 evaluation keeps it ~1e-8.
 //
 // All cross-block sums go through per-block partials reduced in a fixed order
 // by the last block to finish (atomic ticket), so results are deterministic.
@@ -18,6 +24,7 @@
 #include <vector>
 
 #include "laker_device.cuh"
+#include "laker_df.cuh"
 
 namespace {
 
@@ -144,6 +151,85 @@ k_matvec_mat(const T* __restrict__ K, int64_t ldk, int64_t n, double lambda, int
 }
 
 // ---------------------------------------------------------------------------
+// Float64-accurate product with G stored as the float32 pair (hi, lo):
+// w = lambda x + (hi + lo) x in compensated (Dot3) arithmetic on the float32
+// pipes.  8 bytes of G per entry, like float64, but HBM-bound instead of
+// float64-FMA-bound on GB300.  Used for the true residual of mixed solves.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ lk::df2 warp_sum_df(lk::df2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lk::df2 u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = lk::df_add(v, u);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(MV_THREADS)
+k_matvec_df(const float* __restrict__ Khi, const float* __restrict__ Klo, int64_t ldk, int64_t n, double lambda,
+            int64_t chunk, const double* __restrict__ x, double* __restrict__ w, const PcgScalars* sc, int gate) {
+    if (gated_out(sc, gate)) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int64_t r1 = min(n, r0 + rows_per);
+    const int nrows = r1 > r0 ? (int)(r1 - r0) : 0;
+    float2* xs = reinterpret_cast<float2*>(smraw);
+    double* acc = reinterpret_cast<double*>(smraw + chunk * sizeof(float2));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) acc[i] = 0.0;
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t clen = min(chunk, n - c0);
+        const int64_t cpad = (clen + 3) / 4 * 4;
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < cpad; j += blockDim.x) {
+            const int64_t gj = c0 + j;
+            const lk::df2 v = lk::df_from(gj < n ? x[gj] : 0.0);
+            xs[j] = make_float2(v.hi, v.lo);
+        }
+        __syncthreads();
+        const int64_t nv = cpad / 4;
+        for (int rr = wid; rr < nrows; rr += nw) {
+            const float4* rh = reinterpret_cast<const float4*>(Khi + (r0 + rr) * ldk + c0);
+            const float4* rl = reinterpret_cast<const float4*>(Klo + (r0 + rr) * ldk + c0);
+            lk::Dot3 d0, d1;
+            int64_t v = lane;
+            for (; v + 32 < nv; v += 64) {
+                const float4 a0 = __ldcs(rh + v), b0 = __ldcs(rl + v);
+                const float4 a1 = __ldcs(rh + v + 32), b1 = __ldcs(rl + v + 32);
+                const float2* p0 = xs + 4 * v;
+                const float2* p1 = xs + 4 * (v + 32);
+                d0.add({a0.x, b0.x}, {p0[0].x, p0[0].y});
+                d1.add({a1.x, b1.x}, {p1[0].x, p1[0].y});
+                d0.add({a0.y, b0.y}, {p0[1].x, p0[1].y});
+                d1.add({a1.y, b1.y}, {p1[1].x, p1[1].y});
+                d0.add({a0.z, b0.z}, {p0[2].x, p0[2].y});
+                d1.add({a1.z, b1.z}, {p1[2].x, p1[2].y});
+                d0.add({a0.w, b0.w}, {p0[3].x, p0[3].y});
+                d1.add({a1.w, b1.w}, {p1[3].x, p1[3].y});
+            }
+            for (; v < nv; v += 32) {
+                const float4 a0 = __ldcs(rh + v), b0 = __ldcs(rl + v);
+                const float2* p0 = xs + 4 * v;
+                d0.add({a0.x, b0.x}, {p0[0].x, p0[0].y});
+                d0.add({a0.y, b0.y}, {p0[1].x, p0[1].y});
+                d0.add({a0.z, b0.z}, {p0[2].x, p0[2].y});
+                d0.add({a0.w, b0.w}, {p0[3].x, p0[3].y});
+            }
+            const lk::df2 sum = warp_sum_df(lk::df_add(d0.value(), d1.value()));
+            if (lane == 0) acc[rr] += lk::df_to(sum);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        const int64_t gi = r0 + i;
+        w[gi] = fma(lambda, x[gi], acc[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Vector kernels.  Block b owns the contiguous rows [b*R, (b+1)*R).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void row_range(int64_t n, int64_t& r0, int64_t& r1) {
@@ -177,9 +263,16 @@ __device__ void utr_partial(const PT* __restrict__ U, int n_r, int64_t r0, int64
 template <typename PT>
 __device__ void reduce_t(const PT* __restrict__ tpart, int nb, int n_r, PT* __restrict__ t) {
     for (int k = threadIdx.x; k < n_r; k += blockDim.x) {
-        PT a = PT(0);
-        for (int b = 0; b < nb; ++b) a += __ldcg(tpart + (int64_t)b * n_r + k);
-        t[k] = a;
+        PT a0 = PT(0), a1 = PT(0), a2 = PT(0), a3 = PT(0);   // independent chains, fixed order
+        int b = 0;
+        for (; b + 3 < nb; b += 4) {
+            a0 += __ldcg(tpart + (int64_t)(b + 0) * n_r + k);
+            a1 += __ldcg(tpart + (int64_t)(b + 1) * n_r + k);
+            a2 += __ldcg(tpart + (int64_t)(b + 2) * n_r + k);
+            a3 += __ldcg(tpart + (int64_t)(b + 3) * n_r + k);
+        }
+        for (; b < nb; ++b) a0 += __ldcg(tpart + (int64_t)b * n_r + k);
+        t[k] = (a0 + a1) + (a2 + a3);
     }
 }
 
@@ -278,7 +371,7 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
     }
 }
 
-// TR2: r = y - w2 with w2 = (lambda I + G64) alpha; stop test on the true residual.
+// TR2: r = y - w2 with w2 = (lambda I + G) alpha; stop test on the true residual.
 template <typename PT>
 __global__ void __launch_bounds__(VEC_THREADS)
 k_true_residual(int64_t n, const double* __restrict__ y, const double* __restrict__ w2,
@@ -332,14 +425,28 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
         __syncthreads();
         const PT* W = (const PT*)pv.W;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int64_t i = r0 + wid; i < r1; i += nw) {
-            PT a = PT(0);
-            for (int k = lane; k < pv.n_r; k += 32) a += W[i * pv.n_r + k] * ts[k];
+        // two rows per warp in flight
+        for (int64_t i = r0 + 2 * wid; i < r1; i += 2 * nw) {
+            const bool two = (i + 1) < r1;
+            PT a = PT(0), b = PT(0);
+            const PT* w0 = W + i * pv.n_r;
+            const PT* w1 = W + (two ? i + 1 : i) * pv.n_r;
+            for (int k = lane; k < pv.n_r; k += 32) {
+                const PT tk = ts[k];
+                a += w0[k] * tk;
+                b += w1[k] * tk;
+            }
             a = lk::warp_sum(a);
-            const double zi = fma(pv.cinv, r[i], (double)a);
+            b = lk::warp_sum(b);
             if (lane == 0) {
-                z[i] = zi;
-                rz = fma(r[i], zi, rz);
+                const double z0 = fma(pv.cinv, r[i], (double)a);
+                z[i] = z0;
+                rz = fma(r[i], z0, rz);
+                if (two) {
+                    const double z1 = fma(pv.cinv, r[i + 1], (double)b);
+                    z[i + 1] = z1;
+                    rz = fma(r[i + 1], z1, rz);
+                }
             }
         }
     } else {
@@ -414,11 +521,21 @@ struct Workspace {
     PcgScalars* sc;
     unsigned int* ticket;
     int vec_blocks;
+    int pre_blocks;
     int mv_blocks;
 };
 
+// Kernels that produce U^T r partials: few blocks, so the last block's
+// fixed-order reduction of n_r x blocks partials stays short.
 int vec_blocks_for(const laker_ctx* ctx, int64_t n) {
-    int64_t b = (n + 63) / 64;
+    (void)ctx;
+    int64_t b = (n + 255) / 256;
+    b = std::min<int64_t>(b, 64);
+    return (int)std::max<int64_t>(1, b);
+}
+// The preconditioner apply streams W (n x n_r): many blocks.
+int pre_blocks_for(const laker_ctx* ctx, int64_t n) {
+    int64_t b = (n + 15) / 16;
     b = std::min<int64_t>(b, 2 * ctx->num_sms);
     return (int)std::max<int64_t>(1, b);
 }
@@ -451,6 +568,20 @@ laker_status launch_mv(laker_ctx* ctx, const laker_op* op, const T* K, const dou
     return LAKER_OK;
 }
 
+laker_status launch_mv_df(laker_ctx* ctx, const laker_op* op, const double* x, double* w, const PcgScalars* sc,
+                          int gate, int blocks) {
+    const int64_t n = op->n;
+    int64_t chunk = std::min<int64_t>((n + 3) / 4 * 4, (int64_t)(160 * 1024 / sizeof(float2)));
+    chunk = chunk / 4 * 4;
+    const int64_t rows_per = (n + blocks - 1) / blocks;
+    const size_t smem = chunk * sizeof(float2) + rows_per * sizeof(double);
+    if (smem > MV_SMEM_MAX) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "matvec row block too large");
+    k_matvec_df<<<blocks, MV_THREADS, smem, ctx->stream>>>(op->K32, op->K32lo, op->ldk, n, op->lambda, chunk, x, w,
+                                                           sc, gate);
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}
+
 PrecView make_view(const laker_precond* P, bool use32) {
     PrecView v{};
     if (P == nullptr) { v.kind = PRECOND_IDENTITY; return v; }
@@ -466,13 +597,14 @@ PrecView make_view(const laker_precond* P, bool use32) {
 laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws) {
     const int64_t n = op->n;
     ws.vec_blocks = vec_blocks_for(ctx, n);
+    ws.pre_blocks = pre_blocks_for(ctx, n);
     ws.mv_blocks = mv_blocks_for(ctx, n);
     laker_status st;
     double* base = nullptr;
     if ((st = lk_malloc(ctx, (void**)&base, (size_t)6 * n * sizeof(double))) != LAKER_OK) return st;
     ws.r = base; ws.z = base + n; ws.p[0] = base + 2 * n; ws.p[1] = base + 3 * n; ws.w = base + 4 * n;
     ws.w2 = base + 5 * n;
-    const int nb = std::max(ws.vec_blocks, ws.mv_blocks) + 8;
+    const int nb = 4 * ctx->num_sms + 8;   // per-block partials of any of the kernels
     if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
     const int nr = std::max(1, n_r);
     if ((st = lk_malloc(ctx, &ws.tpart, (size_t)ws.vec_blocks * nr * sizeof(double))) != LAKER_OK) return st;
@@ -512,15 +644,13 @@ laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecVie
                                                                       ws.partials, pv, (PT*)ws.tpart, (PT*)ws.t);
     LK_LAUNCHED(ctx);
     if (mixed) {
-        // TR1: w2 = (lambda I + G64) alpha, only when a true residual is due
-        if ((st = launch_mv<double>(ctx, op, op->K64, alpha, nullptr, nullptr, 0, ws.w2, ws.sc, nullptr,
-                                    GATE_TRUE, 0, ws.mv_blocks)) != LAKER_OK)
-            return st;
+        // TR1: w2 = (lambda I + G) alpha in double-float, only when a true residual is due
+        if ((st = launch_mv_df(ctx, op, alpha, ws.w2, ws.sc, GATE_TRUE, ws.mv_blocks)) != LAKER_OK) return st;
         k_true_residual<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.r, ws.sc, ws.partials,
                                                                              pv, (PT*)ws.tpart, (PT*)ws.t);
         LK_LAUNCHED(ctx);
     }
-    k_precond<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
+    k_precond<PT><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
                                                                    (const PT*)ws.t, GATE_RUNNING);
     LK_LAUNCHED(ctx);
     return LAKER_OK;
@@ -529,8 +659,10 @@ laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecVie
 }  // namespace
 
 laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
-    if (op->variant == LAKER_MATRIX_FREE)
-        return mf_matvec_launch(ctx, op, x, nullptr, nullptr, w, nullptr, nullptr, 0, nullptr, nullptr);
+    if (op->variant == LAKER_MATRIX_FREE) {
+        laker_status st = mf_matvec_launch(ctx, op, x, nullptr, nullptr, w, nullptr, nullptr, 0, nullptr, nullptr);
+        return st != LAKER_OK ? st : mf_status(ctx, op);
+    }
     if (op->precision == LAKER_FP64)
         return launch_mv<double>(ctx, op, op->K64, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
                                  mv_blocks_for(ctx, op->n));
@@ -539,8 +671,31 @@ laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x
 }
 
 laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
+    if (op->precision != LAKER_FP64) return launch_mv_df(ctx, op, x, w, nullptr, GATE_NONE, mv_blocks_for(ctx, op->n));
     return launch_mv<double>(ctx, op, op->K64, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
                              mv_blocks_for(ctx, op->n));
+}
+
+laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms) {
+    double* w = nullptr;
+    laker_status st = lk_malloc(ctx, (void**)&w, (size_t)op->n * sizeof(double));
+    if (st != LAKER_OK) return st;
+    cudaEvent_t e0, e1;
+    LK_CUDA(ctx, cudaEventCreate(&e0));
+    LK_CUDA(ctx, cudaEventCreate(&e1));
+    for (int rep = -1; rep < reps && st == LAKER_OK; ++rep) {
+        if (rep == 0) LK_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        st = op_matvec_inner(ctx, op, x, w);
+    }
+    LK_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    LK_CUDA(ctx, cudaEventSynchronize(e1));
+    float t = 0.f;
+    LK_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(w);
+    *ms = (double)t / reps;
+    return st;
 }
 
 laker_status pcg_prepare(laker_ctx* ctx) {
@@ -552,6 +707,7 @@ laker_status pcg_prepare(laker_ctx* ctx) {
                                       (int)MV_SMEM_MAX));
     LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)MV_SMEM_MAX));
+    LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MV_SMEM_MAX));
     return LAKER_OK;
 }
 
@@ -560,7 +716,8 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
     const int vb = vec_blocks_for(ctx, n);
     PrecView pv = make_view(P, P->use32);
     if (P->kind != PRECOND_CCCP) {
-        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, nullptr, GATE_NONE);
+        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr,
+                                                               pv, nullptr, GATE_NONE);
         LK_LAUNCHED(ctx);
         return LAKER_OK;
     }
@@ -574,13 +731,13 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
     if (P->use32) {
         k_utr<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, pv, (float*)tpart, (float*)t, ticket);
         LK_LAUNCHED(ctx);
-        k_precond<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, (const float*)t,
-                                                              GATE_NONE);
+        k_precond<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr,
+                                                              pv, (const float*)t, GATE_NONE);
     } else {
         k_utr<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, pv, (double*)tpart, (double*)t, ticket);
         LK_LAUNCHED(ctx);
-        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, (const double*)t,
-                                                               GATE_NONE);
+        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr,
+                                                               pv, (const double*)t, GATE_NONE);
     }
     LK_LAUNCHED(ctx);
     LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -613,14 +770,16 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
             k_pcg_init<float><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(
                 n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, pv, (float*)ws.tpart, (float*)ws.t, tol);
             LK_LAUNCHED(ctx);
-            k_precond<float><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
-                                                                              (const float*)ws.t, GATE_RUNNING);
+            k_precond<float><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc,
+                                                                              ws.partials, pv, (const float*)ws.t,
+                                                                              GATE_RUNNING);
         } else {
             k_pcg_init<double><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(
                 n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, pv, (double*)ws.tpart, (double*)ws.t, tol);
             LK_LAUNCHED(ctx);
-            k_precond<double><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
-                                                                               (const double*)ws.t, GATE_RUNNING);
+            k_precond<double><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc,
+                                                                               ws.partials, pv, (const double*)ws.t,
+                                                                               GATE_RUNNING);
         }
         LK_LAUNCHED(ctx);
         return LAKER_OK;
@@ -660,6 +819,7 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     cudaFreeHost(flag_host);
+    if (op->variant == LAKER_MATRIX_FREE && (st = mf_status(ctx, op)) != LAKER_OK) { ws_free(ws); return st; }
 
     // final report: float64-accurate residual of the returned alpha
     if ((st = op_matvec_fp64(ctx, op, alpha, ws.w2)) != LAKER_OK) { ws_free(ws); return st; }

@@ -64,6 +64,7 @@ def library() -> ctypes.CDLL:
         "laker_op_destroy": (i32, [vp]),
         "laker_op_matvec": (i32, [vp, vp, vp, vp]),
         "laker_op_matvec_fp64": (i32, [vp, vp, vp, vp]),
+        "laker_op_time_operator": (i32, [vp, vp, vp, i32, ctypes.POINTER(f64)]),
         "laker_fit_preconditioner": (i32, [vp, vp, vp, i32, f64, f64, f64, i32, f64, pvp,
                                            ctypes.POINTER(FitInfo)]),
         "laker_precond_jacobi": (i32, [vp, vp, pvp]),
@@ -198,6 +199,15 @@ def laker_op_matvec(ctx: Context, op: Operator, x: torch.Tensor, w: torch.Tensor
     with ctx:
         ctx.check(fn(ctx.handle, op.handle, _ptr(x, "x", op.n), _ptr(w, "w", op.n)))
     return w
+
+
+def laker_op_time_operator(ctx: Context, op: Operator, x: torch.Tensor, reps: int = 20) -> float:
+    """Average device milliseconds of the operator's main kernel (roofline use)."""
+    ms = ctypes.c_double()
+    with ctx:
+        ctx.check(library().laker_op_time_operator(ctx.handle, op.handle, _ptr(x, "x", op.n), reps,
+                                                   ctypes.byref(ms)))
+    return ms.value
 
 
 def laker_fit_preconditioner(ctx: Context, op: Operator, Z: torch.Tensor, gamma: float = 0.1,

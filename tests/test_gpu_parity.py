@@ -256,3 +256,30 @@ def test_map_double_float_matches_oracle(L, ctx, n, d, m):
     db = inst.y_sigma * (f - fref)
     assert math.sqrt(np.mean(db ** 2)) < 1e-4
     assert rel(f, fref) < 1e-8
+
+
+@pytest.mark.parametrize("n,d", [(100, 16), (1000, 32), (4097, 32), (777, 64)])
+def test_matvec_bf16x3_matrix_free_matches_oracle(L, ctx, n, d):
+    """tcgen05 matrix-free product: split-bf16 logits (float32 accumulate),
+    ex2.approx, float32 row sums; ~1e-6 relative per kernel value."""
+    from tests.gpu_util import dev, host, rel
+    inst = _inst(n, d, 1e-3, 300 + n)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.BF16X3)
+    x = synth.random_vector(n, n)
+    assert rel(host(L.laker_op_matvec(ctx, op, dev(x))), A @ x) < 1e-5
+    assert rel(host(L.laker_op_matvec(ctx, op, dev(x), fp64=True)), A @ x) < 1e-13
+
+
+def test_bf16x3_mixed_solve_reaches_true_tolerance(L, ctx):
+    from tests.gpu_util import dev, host, rel
+    n = 2048
+    inst = _inst(n, 32, 1e-4, 18, layout="clustered")
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    Z = synth.directions(n, 128, 18)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.BF16X3)
+    P = L.laker_fit_preconditioner(ctx, op, dev(Z))
+    alpha, info = L.laker_pcg_solve(ctx, op, P, dev(inst.y), 1e-6, refine_every=20)
+    res = O.relative_residual(A, host(alpha), inst.y)
+    assert res <= 1e-6 * (1 + 1e-6), (res, info)
+    assert info["true_residuals"] >= 1
