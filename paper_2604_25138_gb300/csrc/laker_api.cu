@@ -53,7 +53,8 @@ void free_precond(laker_precond* P) {
     cudaFree(P->D);
     cudaFree(P->U64);
     cudaFree(P->W64);
-    cudaFree(P->U32);
+    cudaFree(P->UT32);
+    cudaFree(P->UT64);
     cudaFree(P->W32);
     cudaFree(P->dinv);
     delete P;

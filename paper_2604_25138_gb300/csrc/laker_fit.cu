@@ -130,6 +130,22 @@ __global__ void k_to_float(int64_t count, const double* __restrict__ x, float* _
     if (i < count) y[i] = (float)x[i];
 }
 
+// UT[k][i] = U[i][k] (n x n_r row-major -> n_r x ldu, zero padding), 32 x 32 tiles.
+template <typename T>
+__global__ void k_transpose(int64_t n, int n_r, int64_t ldu, const double* __restrict__ U, T* __restrict__ UT) {
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+        const int64_t i = i0 + rr, k = k0 + threadIdx.x;
+        tile[rr][threadIdx.x] = (i < n && k < n_r) ? U[i * n_r + k] : 0.0;
+    }
+    __syncthreads();
+    for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
+        const int64_t k = k0 + kk, i = i0 + threadIdx.x;
+        if (k < n_r && i < ldu) UT[k * ldu + i] = (T)tile[threadIdx.x][kk];
+    }
+}
+
 // u_bar_k = u_k / |u_k|  (columns of an n x n_r row-major matrix), fixed-order norms.
 __global__ void k_colnorm(int64_t n, int n_r, const double* __restrict__ U, double* __restrict__ inv) {
     __shared__ double red[8];
@@ -608,13 +624,22 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     P->cinvsqrt = 1.0 / std::sqrt(h.c);
     if ((st = lk_malloc(ctx, (void**)&P->D, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
     LK_CUDA(ctx, cudaMemcpyAsync(P->D, D, nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (op->precision != LAKER_FP64) {
-        if ((st = lk_malloc(ctx, (void**)&P->U32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
-        if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
-        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, U64, P->U32);
-        LK_LAUNCHED(ctx);
-        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, W64, P->W32);
-        LK_LAUNCHED(ctx);
+    // U^T with a padded row pitch for the streaming U^T r of the apply
+    P->ldu = (n + 3) / 4 * 4;
+    {
+        dim3 tb(32, 8), tg((unsigned)((nr + 31) / 32), (unsigned)((P->ldu + 31) / 32));
+        if (op->precision != LAKER_FP64) {
+            if ((st = lk_malloc(ctx, (void**)&P->UT32, (size_t)nr * P->ldu * sizeof(float))) != LAKER_OK) return st;
+            if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+            k_transpose<float><<<tg, tb, 0, s>>>(n, nr, P->ldu, U64, P->UT32);
+            LK_LAUNCHED(ctx);
+            k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, W64, P->W32);
+            LK_LAUNCHED(ctx);
+        } else {
+            if ((st = lk_malloc(ctx, (void**)&P->UT64, (size_t)nr * P->ldu * sizeof(double))) != LAKER_OK) return st;
+            k_transpose<double><<<tg, tb, 0, s>>>(n, nr, P->ldu, U64, P->UT64);
+            LK_LAUNCHED(ctx);
+        }
     }
     LK_CUDA(ctx, cudaStreamSynchronize(s));
     for (void* ptr : {(void*)tmpv, (void*)M, (void*)A, (void*)D, (void*)Dn, (void*)q, (void*)partials, (void*)cn,

@@ -238,61 +238,21 @@ __device__ __forceinline__ void row_range(int64_t n, int64_t& r0, int64_t& r1) {
     r1 = min(n, r0 + R);
 }
 
-// tpart[k] = sum_{i in [r0,r1)} U[i][k] * r[i]  for this block, fixed order.
-template <typename PT>
-__device__ void utr_partial(const PT* __restrict__ U, int n_r, int64_t r0, int64_t r1,
-                            const double* __restrict__ r, PT* __restrict__ tpart, PT* sm) {
-    const int G = (n_r >= (int)blockDim.x) ? 1 : (int)blockDim.x / n_r;
-    const int kth = (int)blockDim.x / G;
-    const int g = threadIdx.x / kth, kt = threadIdx.x % kth;
-    if (g < G) {
-        for (int k = kt; k < n_r; k += kth) {
-            PT a = PT(0);
-            for (int64_t i = r0 + g; i < r1; i += G) a += U[i * n_r + k] * (PT)r[i];
-            sm[g * n_r + k] = a;
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < n_r; k += blockDim.x) {
-        PT a = PT(0);
-        for (int gg = 0; gg < G; ++gg) a += sm[gg * n_r + k];
-        tpart[k] = a;
-    }
-}
-
-template <typename PT>
-__device__ void reduce_t(const PT* __restrict__ tpart, int nb, int n_r, PT* __restrict__ t) {
-    for (int k = threadIdx.x; k < n_r; k += blockDim.x) {
-        PT a0 = PT(0), a1 = PT(0), a2 = PT(0), a3 = PT(0);   // independent chains, fixed order
-        int b = 0;
-        for (; b + 3 < nb; b += 4) {
-            a0 += __ldcg(tpart + (int64_t)(b + 0) * n_r + k);
-            a1 += __ldcg(tpart + (int64_t)(b + 1) * n_r + k);
-            a2 += __ldcg(tpart + (int64_t)(b + 2) * n_r + k);
-            a3 += __ldcg(tpart + (int64_t)(b + 3) * n_r + k);
-        }
-        for (; b < nb; ++b) a0 += __ldcg(tpart + (int64_t)b * n_r + k);
-        t[k] = (a0 + a1) + (a2 + a3);
-    }
-}
-
 struct PrecView {
     int kind;
     int n_r;
+    int64_t ldu;
     double cinv;
-    const void* U;
-    const void* W;
+    const void* UT;   // n_r x ldu, U transposed
+    const void* W;    // n x n_r
     const double* dinv;
 };
 
-// INIT: alpha = 0, r = y, p = 0, |y|^2, t = U^T y.
-template <typename PT>
+// INIT: alpha = 0, r = y, p = 0, |y|^2.
 __global__ void __launch_bounds__(VEC_THREADS)
 k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, double* __restrict__ r,
-           double* __restrict__ p0, PcgScalars* sc, double* __restrict__ partials, PrecView pv,
-           PT* __restrict__ tpart, PT* __restrict__ t, double tol) {
+           double* __restrict__ p0, PcgScalars* sc, double* __restrict__ partials, double tol) {
     __shared__ double red[VEC_THREADS / 32];
-    __shared__ PT sm[1024];
     int64_t r0, r1;
     row_range(n, r0, r1);
     double yy = 0.0;
@@ -303,14 +263,10 @@ k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, 
         p0[i] = 0.0;
         yy = fma(yi, yi, yy);
     }
-    __syncthreads();
-    if (pv.kind == PRECOND_CCCP)
-        utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
     yy = lk::block_sum(yy, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = yy;
     if (lk::last_block(&sc->ticket[1])) {
         const double tot = lk::sum_partials(partials, gridDim.x, red);
-        if (pv.kind == PRECOND_CCCP) reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
         if (threadIdx.x == 0) {
             sc->yy = tot;
             sc->rr = tot;
@@ -327,15 +283,12 @@ k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, 
     }
 }
 
-// UPD: alpha += delta p, r -= delta w, |r|^2, t = U^T r; stop / refinement decisions.
-template <typename PT>
+// UPD: alpha += delta p, r -= delta w, |r|^2; stop / refinement decisions.
 __global__ void __launch_bounds__(VEC_THREADS)
-k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__ w,
-             double* __restrict__ alpha, double* __restrict__ r, PcgScalars* sc,
-             double* __restrict__ partials, PrecView pv, PT* __restrict__ tpart, PT* __restrict__ t) {
+k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ alpha,
+             double* __restrict__ r, PcgScalars* sc, double* __restrict__ partials) {
     if (gated_out(sc, GATE_RUNNING)) return;
     __shared__ double red[VEC_THREADS / 32];
-    __shared__ PT sm[1024];
     int64_t r0, r1;
     row_range(n, r0, r1);
     const double delta = sc->delta;
@@ -346,14 +299,10 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
         r[i] = ri;
         rr = fma(ri, ri, rr);
     }
-    __syncthreads();
-    if (pv.kind == PRECOND_CCCP)
-        utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
     rr = lk::block_sum(rr, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = rr;
     if (lk::last_block(&sc->ticket[2])) {
         const double tot = lk::sum_partials(partials, gridDim.x, red);
-        if (pv.kind == PRECOND_CCCP) reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
         if (threadIdx.x == 0) {
             sc->rr = tot;
             const int it = sc->iters;
@@ -372,14 +321,11 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
 }
 
 // TR2: r = y - w2 with w2 = (lambda I + G) alpha; stop test on the true residual.
-template <typename PT>
 __global__ void __launch_bounds__(VEC_THREADS)
-k_true_residual(int64_t n, const double* __restrict__ y, const double* __restrict__ w2,
-                double* __restrict__ r, PcgScalars* sc, double* __restrict__ partials, PrecView pv,
-                PT* __restrict__ tpart, PT* __restrict__ t) {
+k_true_residual(int64_t n, const double* __restrict__ y, const double* __restrict__ w2, double* __restrict__ r,
+                PcgScalars* sc, double* __restrict__ partials) {
     if (gated_out(sc, GATE_TRUE)) return;
     __shared__ double red[VEC_THREADS / 32];
-    __shared__ PT sm[1024];
     int64_t r0, r1;
     row_range(n, r0, r1);
     double rr = 0.0;
@@ -388,14 +334,10 @@ k_true_residual(int64_t n, const double* __restrict__ y, const double* __restric
         r[i] = ri;
         rr = fma(ri, ri, rr);
     }
-    __syncthreads();
-    if (pv.kind == PRECOND_CCCP)
-        utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
     rr = lk::block_sum(rr, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = rr;
     if (lk::last_block(&sc->ticket[3])) {
         const double tot = lk::sum_partials(partials, gridDim.x, red);
-        if (pv.kind == PRECOND_CCCP) reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
         if (threadIdx.x == 0) {
             sc->rr = tot;
             sc->rr_true = tot;
@@ -409,7 +351,56 @@ k_true_residual(int64_t n, const double* __restrict__ y, const double* __restric
     }
 }
 
-// PRE: z = P r, r^T z, beta.
+// UTR: t_k = sum_i U_ik r_i.  One block per k streams row k of U^T (padded
+// pitch ldu, zeros past n) with 16-byte loads; the block's threads stride over
+// the row, keep two independent sums each, and reduce in a fixed order.
+template <typename PT> struct UtrVec;
+template <> struct UtrVec<float> { using type = float4; static constexpr int N = 4; };
+template <> struct UtrVec<double> { using type = double2; static constexpr int N = 2; };
+
+__device__ __forceinline__ float dot_vec(const float4& u, const double* r) {
+    const double2 r01 = *reinterpret_cast<const double2*>(r);
+    const double2 r23 = *reinterpret_cast<const double2*>(r + 2);
+    return fmaf(u.x, (float)r01.x, fmaf(u.y, (float)r01.y, fmaf(u.z, (float)r23.x, u.w * (float)r23.y)));
+}
+__device__ __forceinline__ double dot_vec(const double2& u, const double* r) {
+    const double2 rr = *reinterpret_cast<const double2*>(r);
+    return fma(u.x, rr.x, u.y * rr.y);
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(256)
+k_utr(int64_t n, PrecView pv, const double* __restrict__ r, PT* __restrict__ t, const PcgScalars* sc, int gate) {
+    if (gated_out(sc, gate)) return;
+    __shared__ PT red[8];
+    constexpr int VN = UtrVec<PT>::N;
+    using V = typename UtrVec<PT>::type;
+    const int k = blockIdx.x;
+    const V* u = reinterpret_cast<const V*>((const PT*)pv.UT + (int64_t)k * pv.ldu);
+    const int64_t nfull = n / VN;                 // vectors entirely inside [0, n)
+    PT a0 = PT(0), a1 = PT(0);
+    int64_t v = threadIdx.x;
+    for (; v + 256 < nfull; v += 512) {
+        const V u0 = __ldg(u + v), u1 = __ldg(u + v + 256);
+        a0 += dot_vec(u0, r + v * VN);
+        a1 += dot_vec(u1, r + (v + 256) * VN);
+    }
+    for (; v < nfull; v += 256) a0 += dot_vec(__ldg(u + v), r + v * VN);
+    const PT* us = (const PT*)pv.UT + (int64_t)k * pv.ldu;
+    for (int64_t i = nfull * VN + threadIdx.x; i < n; i += 256) a1 += us[i] * (PT)r[i];
+    PT a = lk::warp_sum(a0 + a1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        PT s = PT(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        t[k] = s;
+    }
+}
+
+// PRE: z = P r, r^T z, beta.  CCCP: z_i = c^-1/2 r_i + sum_k W_ik t_k, four
+// rows per warp in flight.
 template <typename PT>
 __global__ void __launch_bounds__(VEC_THREADS)
 k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgScalars* sc,
@@ -425,27 +416,22 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
         __syncthreads();
         const PT* W = (const PT*)pv.W;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        // two rows per warp in flight
-        for (int64_t i = r0 + 2 * wid; i < r1; i += 2 * nw) {
-            const bool two = (i + 1) < r1;
-            PT a = PT(0), b = PT(0);
-            const PT* w0 = W + i * pv.n_r;
-            const PT* w1 = W + (two ? i + 1 : i) * pv.n_r;
+        for (int64_t i = r0 + 4 * wid; i < r1; i += 4 * nw) {
+            const int nrow = (r1 - i < 4) ? (int)(r1 - i) : 4;
+            PT acc[4] = {PT(0), PT(0), PT(0), PT(0)};
             for (int k = lane; k < pv.n_r; k += 32) {
                 const PT tk = ts[k];
-                a += w0[k] * tk;
-                b += w1[k] * tk;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nrow) acc[q] += W[(i + q) * pv.n_r + k] * tk;
             }
-            a = lk::warp_sum(a);
-            b = lk::warp_sum(b);
-            if (lane == 0) {
-                const double z0 = fma(pv.cinv, r[i], (double)a);
-                z[i] = z0;
-                rz = fma(r[i], z0, rz);
-                if (two) {
-                    const double z1 = fma(pv.cinv, r[i + 1], (double)b);
-                    z[i + 1] = z1;
-                    rz = fma(r[i + 1], z1, rz);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const PT a = lk::warp_sum(acc[q]);
+                if (lane == 0 && q < nrow) {
+                    const double zi = fma(pv.cinv, r[i + q], (double)a);
+                    z[i + q] = zi;
+                    rz = fma(r[i + q], zi, rz);
                 }
             }
         }
@@ -496,28 +482,12 @@ k_resid_norm(int64_t n, const double* __restrict__ y, const double* __restrict__
     }
 }
 
-// standalone U^T r  (preconditioner apply outside a solve)
-template <typename PT>
-__global__ void __launch_bounds__(VEC_THREADS)
-k_utr(int64_t n, const double* __restrict__ r, PrecView pv, PT* __restrict__ tpart, PT* __restrict__ t,
-      unsigned int* ticket) {
-    __shared__ PT sm[1024];
-    int64_t r0, r1;
-    row_range(n, r0, r1);
-    utr_partial<PT>((const PT*)pv.U, pv.n_r, r0, r1, r, tpart + (int64_t)blockIdx.x * pv.n_r, sm);
-    if (threadIdx.x == 0) { /* partial written by utr_partial */ }
-    if (lk::last_block(ticket)) {
-        reduce_t<PT>(tpart, gridDim.x, pv.n_r, t);
-        if (threadIdx.x == 0) *ticket = 0;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 struct Workspace {
     double *r, *z, *p[2], *w, *w2, *partials;
-    void *tpart, *t;
+    void* t;
     PcgScalars* sc;
     unsigned int* ticket;
     int vec_blocks;
@@ -525,12 +495,10 @@ struct Workspace {
     int mv_blocks;
 };
 
-// Kernels that produce U^T r partials: few blocks, so the last block's
-// fixed-order reduction of n_r x blocks partials stays short.
+// Elementwise vector kernels with a scalar reduction.
 int vec_blocks_for(const laker_ctx* ctx, int64_t n) {
-    (void)ctx;
     int64_t b = (n + 255) / 256;
-    b = std::min<int64_t>(b, 64);
+    b = std::min<int64_t>(b, 2 * ctx->num_sms);
     return (int)std::max<int64_t>(1, b);
 }
 // The preconditioner apply streams W (n x n_r): many blocks.
@@ -587,11 +555,21 @@ PrecView make_view(const laker_precond* P, bool use32) {
     if (P == nullptr) { v.kind = PRECOND_IDENTITY; return v; }
     v.kind = P->kind;
     v.n_r = P->n_r;
+    v.ldu = P->ldu;
     v.cinv = P->cinvsqrt;
-    v.U = use32 ? (const void*)P->U32 : (const void*)P->U64;
+    v.UT = use32 ? (const void*)P->UT32 : (const void*)P->UT64;
     v.W = use32 ? (const void*)P->W32 : (const void*)P->W64;
     v.dinv = P->dinv;
     return v;
+}
+
+template <typename PT>
+laker_status launch_utr(laker_ctx* ctx, int64_t n, const PrecView& pv, const double* r, PT* t, const PcgScalars* sc,
+                        int gate) {
+    if (pv.kind != PRECOND_CCCP) return LAKER_OK;
+    k_utr<PT><<<(unsigned)pv.n_r, 256, 0, ctx->stream>>>(n, pv, r, t, sc, gate);
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
 }
 
 laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws) {
@@ -607,7 +585,6 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
     const int nb = 4 * ctx->num_sms + 8;   // per-block partials of any of the kernels
     if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
     const int nr = std::max(1, n_r);
-    if ((st = lk_malloc(ctx, &ws.tpart, (size_t)ws.vec_blocks * nr * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, &ws.t, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&ws.sc, sizeof(PcgScalars))) != LAKER_OK) return st;
     LK_CUDA(ctx, cudaMemsetAsync(ws.sc, 0, sizeof(PcgScalars), ctx->stream));
@@ -617,7 +594,6 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
 void ws_free(Workspace& ws) {
     cudaFree(ws.r);
     cudaFree(ws.partials);
-    cudaFree(ws.tpart);
     cudaFree(ws.t);
     cudaFree(ws.sc);
 }
@@ -640,16 +616,15 @@ laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecVie
                               ws.mv_blocks);
     }
     if (st != LAKER_OK) return st;
-    k_pcg_update<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, pout, ws.w, alpha, ws.r, ws.sc,
-                                                                      ws.partials, pv, (PT*)ws.tpart, (PT*)ws.t);
+    k_pcg_update<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, pout, ws.w, alpha, ws.r, ws.sc, ws.partials);
     LK_LAUNCHED(ctx);
     if (mixed) {
         // TR1: w2 = (lambda I + G) alpha in double-float, only when a true residual is due
         if ((st = launch_mv_df(ctx, op, alpha, ws.w2, ws.sc, GATE_TRUE, ws.mv_blocks)) != LAKER_OK) return st;
-        k_true_residual<PT><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.r, ws.sc, ws.partials,
-                                                                             pv, (PT*)ws.tpart, (PT*)ws.t);
+        k_true_residual<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.r, ws.sc, ws.partials);
         LK_LAUNCHED(ctx);
     }
+    if ((st = launch_utr<PT>(ctx, n, pv, ws.r, (PT*)ws.t, ws.sc, GATE_RUNNING)) != LAKER_OK) return st;
     k_precond<PT><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
                                                                    (const PT*)ws.t, GATE_RUNNING);
     LK_LAUNCHED(ctx);
@@ -713,38 +688,35 @@ laker_status pcg_prepare(laker_ctx* ctx) {
 
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z) {
     const int64_t n = P->n;
-    const int vb = vec_blocks_for(ctx, n);
+    const int vb = pre_blocks_for(ctx, n);
     PrecView pv = make_view(P, P->use32);
     if (P->kind != PRECOND_CCCP) {
-        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr,
-                                                               pv, nullptr, GATE_NONE);
+        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, nullptr, GATE_NONE);
         LK_LAUNCHED(ctx);
         return LAKER_OK;
     }
-    void *tpart = nullptr, *t = nullptr;
-    unsigned int* ticket = nullptr;
+    void* t = nullptr;
+    double* ra = nullptr;
     laker_status st;
-    if ((st = lk_malloc(ctx, &tpart, (size_t)vb * P->n_r * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, &t, (size_t)P->n_r * sizeof(double))) != LAKER_OK) return st;
-    if ((st = lk_malloc(ctx, (void**)&ticket, sizeof(unsigned int))) != LAKER_OK) return st;
-    LK_CUDA(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned int), ctx->stream));
+    if (reinterpret_cast<uintptr_t>(r) & 15) {   // the U^T r kernel reads r with 16-byte loads
+        if ((st = lk_malloc(ctx, (void**)&ra, (size_t)n * sizeof(double))) != LAKER_OK) { cudaFree(t); return st; }
+        LK_CUDA(ctx, cudaMemcpyAsync(ra, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        r = ra;
+    }
     if (P->use32) {
-        k_utr<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, pv, (float*)tpart, (float*)t, ticket);
-        LK_LAUNCHED(ctx);
-        k_precond<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr,
-                                                              pv, (const float*)t, GATE_NONE);
+        st = launch_utr<float>(ctx, n, pv, r, (float*)t, nullptr, GATE_NONE);
+        k_precond<float><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, (const float*)t, GATE_NONE);
     } else {
-        k_utr<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, pv, (double*)tpart, (double*)t, ticket);
-        LK_LAUNCHED(ctx);
-        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr,
-                                                               pv, (const double*)t, GATE_NONE);
+        st = launch_utr<double>(ctx, n, pv, r, (double*)t, nullptr, GATE_NONE);
+        k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, (const double*)t,
+                                                               GATE_NONE);
     }
     LK_LAUNCHED(ctx);
     LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    cudaFree(tpart);
     cudaFree(t);
-    cudaFree(ticket);
-    return LAKER_OK;
+    cudaFree(ra);
+    return st;
 }
 
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
@@ -756,7 +728,8 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     laker_status st = ws_alloc(ctx, op, P ? P->n_r : 0, ws);
     if (st != LAKER_OK) return st;
     PrecView pv = make_view(P, use32);
-    if (P && P->kind == PRECOND_CCCP && use32 && (P->U32 == nullptr || P->W32 == nullptr)) {
+    if (P && P->kind == PRECOND_CCCP && ((use32 && (P->UT32 == nullptr || P->W32 == nullptr)) ||
+                                          (!use32 && P->UT64 == nullptr))) {
         ws_free(ws);
         return set_error(ctx, LAKER_ERR_ARG, "preconditioner has no float32 factors for this operator");
     }
@@ -766,20 +739,17 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     LK_CUDA(ctx, cudaMemcpyAsync(ws.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
 
     auto run_init = [&]() -> laker_status {
+        k_pcg_init<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, tol);
+        LK_LAUNCHED(ctx);
+        laker_status s2;
         if (use32) {
-            k_pcg_init<float><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(
-                n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, pv, (float*)ws.tpart, (float*)ws.t, tol);
-            LK_LAUNCHED(ctx);
-            k_precond<float><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc,
-                                                                              ws.partials, pv, (const float*)ws.t,
-                                                                              GATE_RUNNING);
+            if ((s2 = launch_utr<float>(ctx, n, pv, ws.r, (float*)ws.t, ws.sc, GATE_RUNNING)) != LAKER_OK) return s2;
+            k_precond<float><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
+                                                                              (const float*)ws.t, GATE_RUNNING);
         } else {
-            k_pcg_init<double><<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(
-                n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, pv, (double*)ws.tpart, (double*)ws.t, tol);
-            LK_LAUNCHED(ctx);
-            k_precond<double><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc,
-                                                                               ws.partials, pv, (const double*)ws.t,
-                                                                               GATE_RUNNING);
+            if ((s2 = launch_utr<double>(ctx, n, pv, ws.r, (double*)ws.t, ws.sc, GATE_RUNNING)) != LAKER_OK) return s2;
+            k_precond<double><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,
+                                                                               (const double*)ws.t, GATE_RUNNING);
         }
         LK_LAUNCHED(ctx);
         return LAKER_OK;
