@@ -31,12 +31,13 @@
 
 namespace {
 
-constexpr int MF_ROWS = 128;        // rows per CTA = tensor-memory lanes
-constexpr int MF_COLS = 128;        // columns per tile = MMA N
-constexpr int MF_STAGES = 4;
-constexpr int MF_EPI_WARPS = 8;
+constexpr int MF_B = 128;            // block edge: tensor-memory lanes (j) = MMA N (i)
+constexpr int MF_EPW = 4;            // epilogue warps per tensor-memory lane quadrant
+constexpr int MF_EPI_WARPS = 4 * MF_EPW;
+constexpr int MF_WCOLS = MF_B / MF_EPW;   // i columns per epilogue warp
 constexpr int MF_THREADS = (MF_EPI_WARPS + 2) * 32;
-constexpr uint32_t MF_TMEM_COLS = 2 * MF_COLS;
+constexpr int MF_NACC = 4;           // accumulator ring in tensor memory
+constexpr uint32_t MF_TMEM_COLS = MF_NACC * MF_B;   // all 512 columns: one CTA per SM
 constexpr long long MF_SPIN_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -65,16 +66,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: false after MF_SPIN_CYCLES or once another thread raised *err.
+// The error word (a global load, hundreds of cycles) and the clock are read
+// only every 256 failed polls, so that a completed phase is seen at once.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*(volatile int*)err) return false;
-        if (clock64() - t0 > MF_SPIN_CYCLES) {
-            atomicExch(err, LAKER_ERR_TIMEOUT);
-            return false;
+    for (uint32_t spins = 1;; ++spins) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spins & 255u) == 0) {
+            if (*(volatile int*)err) return false;
+            if (clock64() - t0 > MF_SPIN_CYCLES) {
+                atomicExch(err, LAKER_ERR_TIMEOUT);
+                return false;
+            }
         }
     }
-    return true;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -121,20 +127,25 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// 32 consecutive float32 columns of this warp's 32 tensor-memory lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
+// 16 consecutive float32 columns of this warp's 32 tensor-memory lanes; the
+// values may be read only after tmem_wait() has returned them.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// Waits for every outstanding tcgen05.ld of the warp; the registers of `r`
+// pass through the wait so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -143,29 +154,53 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+template <int DPAD>
+struct MfCfg {
+    static constexpr int STAGES = DPAD >= 64 ? 4 : 8;      // ring of streamed j-block operand tiles
+    static constexpr int TILE_BYTES = MF_B * DPAD * 2;     // one bf16 operand tile (128 rows)
+    static constexpr int SWZ = DPAD * 2;                    // swizzle span = row bytes
+};
+
 struct MfSmem {
-    // operand tiles first (1024-byte aligned by construction)
-    // [A_hi][A_lo][stage0 B_hi][stage0 B_lo]...[stage S-1 B_lo]
-    uint64_t full[MF_STAGES];
-    uint64_t empty[MF_STAGES];
-    uint64_t tfull[2];
-    uint64_t tempty[2];
-    uint64_t afull;
-    uint64_t aempty;
+    uint64_t full[8];
+    uint64_t empty[8];
+    uint64_t tfull[MF_NACC];
+    uint64_t tempty[MF_NACC];
+    uint64_t bfull;
+    uint64_t bempty;
     uint32_t tmem_base;
 };
 
-// Static schedule: the T = row_blocks x col_tiles tiles, in row-block-major
-// order, are split into G equal contiguous ranges, one per CTA (2 CTAs per SM,
-// one wave).  A range crossing a row-block boundary is processed as segments;
-// each segment's row sums go to part[((rb * slots + slot) * 2 + half) * 128 + r]
-// with slot = CTA index - first CTA touching row block rb.
+// Symmetric tile schedule.  With nb blocks of 128 indices, block row I owns
+// the tiles (I, J = (I + k) mod nb) for k = 0 .. len(I) - 1: k = 0 is the
+// diagonal tile and every unordered pair of distinct blocks appears exactly
+// once (distances 1 .. (nb - 1) / 2 for every row, and distance nb / 2 only
+// for rows I < nb / 2 when nb is even).  The T tiles, row-major in (I, k),
+// are split into G equal contiguous ranges, one per CTA (one per SM); a range
+// crossing block rows is processed as segments, one per block row.
 struct MfSched {
     int64_t T;
+    int nb;
+    int base;    // len(I) = base + (I < half)
+    int half;
     int G;
-    int CT;      // column tiles per row block
-    int slots;   // max CTAs touching one row block
+    int slots;   // max CTAs sharing one block row
 };
+__host__ __device__ __forceinline__ int mf_row_len(int I, const MfSched& s) { return s.base + (I < s.half ? 1 : 0); }
+__host__ __device__ __forceinline__ int64_t mf_row_start(int I, const MfSched& s) {
+    return I < s.half ? (int64_t)I * (s.base + 1)
+                      : (int64_t)s.half * (s.base + 1) + (int64_t)(I - s.half) * s.base;
+}
+__host__ __device__ __forceinline__ void mf_tile(int64_t x, const MfSched& s, int& I, int& k) {
+    const int64_t x0 = (int64_t)s.half * (s.base + 1);
+    if (x < x0) {
+        I = (int)(x / (s.base + 1));
+        k = (int)(x % (s.base + 1));
+    } else {
+        I = s.half + (int)((x - x0) / s.base);
+        k = (int)((x - x0) % s.base);
+    }
+}
 __host__ __device__ __forceinline__ int64_t mf_tile_begin(int64_t g, const MfSched& s) { return g * s.T / s.G; }
 __host__ __device__ __forceinline__ int mf_owner(int64_t x, const MfSched& s) {
     int g = (int)((x * s.G) / s.T);
@@ -174,35 +209,96 @@ __host__ __device__ __forceinline__ int mf_owner(int64_t x, const MfSched& s) {
     return g;
 }
 
+// One 16-column chunk of the epilogue: e = 2^logit; the fixed block's row
+// sums take e * p_j (j = this lane), the streamed block's sums take e * p_i.
+// Pairs of columns go through the packed float32x2 FMA.
+template <bool DIAG>
+__device__ __forceinline__ void mf_chunk(const uint32_t* v, float2* acc, const float4* pI4, float pj, float2* sJ) {
+    const float2 pjj = make_float2(pj, pj);
+    float2 pI[8];
+    if (!DIAG) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 t = __ldg(pI4 + u);
+            pI[2 * u] = make_float2(t.x, t.y);
+            pI[2 * u + 1] = make_float2(t.z, t.w);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const float2 e = make_float2(ex2_approx(__uint_as_float(v[2 * m])), ex2_approx(__uint_as_float(v[2 * m + 1])));
+        acc[m] = __ffma2_rn(e, pjj, acc[m]);
+        if (!DIAG) sJ[m & 1] = __ffma2_rn(e, pI[m], sJ[m & 1]);
+    }
+}
+
+// Sum of a[c] over the 32 lanes for the 32 columns c, by recursive halving:
+// afterwards lane L holds the sum of column L in a[0].
+__device__ __forceinline__ void mf_lane_reduce(float* a, int lane) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s, H = 16 >> s;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const float send = up ? a[m] : a[m + H];
+            const float keep = up ? a[m + H] : a[m];
+            a[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void mf_tile_epilogue(uint32_t tcol, float2* acc, const float4* pI4, float pj, float2* sJ) {
+    static_assert(MF_WCOLS == 32, "two 16-column chunks per warp");
+    uint32_t v[16];
+    tmem_ld16(tcol, v);
+    tmem_wait(v);
+    mf_chunk<DIAG>(v, acc, pI4, pj, sJ);
+    tmem_ld16(tcol + 16, v);
+    tmem_wait(v);
+    mf_chunk<DIAG>(v, acc + 8, pI4 + 4, pj, sJ);
+}
+
+// Tile (I, J): logits D[j][i] = q'_j . q'_i for the 128 j of block J
+// (tensor-memory lanes, MMA M) and the 128 i of block I (columns, MMA N).
+// Epilogue warp (quadrant q, part h) owns lanes 32q..32q+31 and columns
+// 32h..32h+31: it accumulates the block-I row sums over its lanes in
+// registers for the whole segment, and writes the block-J sums of an
+// off-diagonal tile to colpart[(x * MF_EPW + h) * 128 + j].  At the end of a
+// segment the row sums are reduced over the lanes and stored to
+// rowpart[((I * slots + slot) * 4 + q) * 128 + i].
 template <int DPAD>
-__global__ void __launch_bounds__(MF_THREADS, 2)
+__global__ void __launch_bounds__(MF_THREADS, 1)
 k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-            const float* __restrict__ pf, MfSched sch, float* __restrict__ part, int* __restrict__ err,
-            const PcgScalars* sc) {
+            const float* __restrict__ pf, MfSched sch, float* __restrict__ rowpart, float* __restrict__ colpart,
+            int* __restrict__ err, const PcgScalars* sc) {
     if (sc != nullptr && *(volatile const int*)&sc->converged) return;   // uniform: fixed during the kernel
-    constexpr int TILE_BYTES = MF_ROWS * DPAD * 2;             // one bf16 operand tile
-    constexpr int SWZ = DPAD * 2;                              // swizzle span = row bytes
+    using C = MfCfg<DPAD>;
+    constexpr int TILE = C::TILE_BYTES;
     extern __shared__ __align__(1024) unsigned char mf_smem_raw[];
     unsigned char* base = mf_smem_raw;
     {   // align the dynamic window to 1024 bytes (swizzle-pattern repeat)
         const uint32_t a = smem_u32(base);
         base += (1024 - (a & 1023)) & 1023;
     }
-    unsigned char* sA_hi = base;
-    unsigned char* sA_lo = base + TILE_BYTES;
-    unsigned char* sB = base + 2 * TILE_BYTES;                 // stage s: hi at 2s, lo at 2s+1
-    MfSmem* S = reinterpret_cast<MfSmem*>(base + (2 + 2 * MF_STAGES) * TILE_BYTES);
+    unsigned char* sB_hi = base;                  // fixed block I
+    unsigned char* sB_lo = base + TILE;
+    unsigned char* sA = base + 2 * TILE;          // stage s: hi at 2s, lo at 2s + 1 (streamed block J)
+    MfSmem* S = reinterpret_cast<MfSmem*>(base + (2 + 2 * C::STAGES) * TILE);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x;
     const int64_t t0 = mf_tile_begin(g, sch);
     const int ntiles = (int)(mf_tile_begin(g + 1, sch) - t0);
+    int I0 = 0, k0 = 0;
+    mf_tile(t0, sch, I0, k0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < MF_STAGES; ++s) { mbar_init(&S->full[s], 1); mbar_init(&S->empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { mbar_init(&S->tfull[a], 1); mbar_init(&S->tempty[a], MF_EPI_WARPS); }
-        mbar_init(&S->afull, 1);
-        mbar_init(&S->aempty, 1);
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(&S->full[s], 1); mbar_init(&S->empty[s], 1); }
+        for (int a = 0; a < MF_NACC; ++a) { mbar_init(&S->tfull[a], 1); mbar_init(&S->tempty[a], MF_EPI_WARPS); }
+        mbar_init(&S->bfull, 1);
+        mbar_init(&S->bempty, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == MF_EPI_WARPS + 1) {
@@ -219,37 +315,35 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
     if (warp == MF_EPI_WARPS) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            int issued = 0, seg = 0, cur_rb = -1;
-            bool ok = true;
-            for (int it = 0; ok && it < ntiles; ++it) {
-                const int64_t x = t0 + it;
-                const int rb = (int)(x / sch.CT), ct = (int)(x % sch.CT);
-                if (rb != cur_rb) {   // new segment: reload the row-block operand once it is free
-                    if (seg > 0 && !mbar_wait(&S->aempty, (seg - 1) & 1, err)) { ok = false; break; }
-                    mbar_expect_tx(&S->afull, 2 * TILE_BYTES);
-                    tma_load_2d(sA_hi, &map_hi, &S->afull, 0, rb * MF_ROWS);
-                    tma_load_2d(sA_lo, &map_lo, &S->afull, 0, rb * MF_ROWS);
-                    cur_rb = rb;
+            int issued = 0, seg = 0, I = I0, k = k0;
+            for (int it = 0; it < ntiles; ++it) {
+                if (it == 0 || k == 0) {   // new segment: reload the fixed block once the MMAs released it
+                    if (seg > 0 && !mbar_wait(&S->bempty, (seg - 1) & 1, err)) break;
+                    mbar_expect_tx(&S->bfull, 2 * TILE);
+                    tma_load_2d(sB_hi, &map_hi, &S->bfull, 0, I * MF_B);
+                    tma_load_2d(sB_lo, &map_lo, &S->bfull, 0, I * MF_B);
                     ++seg;
                 }
-                const int st = it % MF_STAGES;
-                const uint32_t ph = (it / MF_STAGES) & 1;
-                if (!mbar_wait(&S->empty[st], ph ^ 1, err)) { ok = false; break; }
-                unsigned char* b = sB + 2 * st * TILE_BYTES;
-                mbar_expect_tx(&S->full[st], 2 * TILE_BYTES);
-                tma_load_2d(b, &map_hi, &S->full[st], 0, ct * MF_COLS);
-                tma_load_2d(b + TILE_BYTES, &map_lo, &S->full[st], 0, ct * MF_COLS);
+                const int st = it % C::STAGES;
+                const uint32_t ph = (it / C::STAGES) & 1;
+                if (!mbar_wait(&S->empty[st], ph ^ 1, err)) break;
+                const int J = (I + k) % sch.nb;
+                unsigned char* a = sA + 2 * st * TILE;
+                mbar_expect_tx(&S->full[st], 2 * TILE);
+                tma_load_2d(a, &map_hi, &S->full[st], 0, J * MF_B);
+                tma_load_2d(a + TILE, &map_lo, &S->full[st], 0, J * MF_B);
                 issued = it + 1;
+                if (++k == mf_row_len(I, sch)) { ++I; k = 0; }
             }
             // drain: every copy this CTA issued has landed before it may exit
             if (seg > 0) {
                 const long long c0 = clock64();
-                while (!mbar_try_wait(&S->afull, (seg - 1) & 1) && clock64() - c0 < MF_SPIN_CYCLES) {
+                while (!mbar_try_wait(&S->bfull, (seg - 1) & 1) && clock64() - c0 < MF_SPIN_CYCLES) {
                 }
             }
-            for (int it = max(0, issued - MF_STAGES); it < issued; ++it) {
+            for (int it = max(0, issued - C::STAGES); it < issued; ++it) {
                 const long long c0 = clock64();
-                while (!mbar_try_wait(&S->full[it % MF_STAGES], (it / MF_STAGES) & 1) &&
+                while (!mbar_try_wait(&S->full[it % C::STAGES], (it / C::STAGES) & 1) &&
                        clock64() - c0 < MF_SPIN_CYCLES) {
                 }
             }
@@ -257,85 +351,91 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
     } else if (warp == MF_EPI_WARPS + 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = instr_desc_bf16(MF_ROWS, MF_COLS);
-            int seg = 0, cur_rb = -1;
+            constexpr uint32_t idesc = instr_desc_bf16(MF_B, MF_B);
+            int seg = 0, I = I0, k = k0;
             for (int it = 0; it < ntiles; ++it) {
-                const int rb = (int)((t0 + it) / sch.CT);
-                if (rb != cur_rb) {
-                    if (seg > 0) umma_commit(&S->aempty);       // previous segment's MMAs release A
-                    if (!mbar_wait(&S->afull, seg & 1, err)) break;
-                    cur_rb = rb;
+                if (it == 0 || k == 0) {
+                    if (seg > 0) umma_commit(&S->bempty);       // previous segment's MMAs release block I
+                    if (!mbar_wait(&S->bfull, seg & 1, err)) break;
                     ++seg;
                 }
-                const int st = it % MF_STAGES;
-                const uint32_t ph = (it / MF_STAGES) & 1;
-                const int acc = it & 1;
-                const uint32_t aph = (it >> 1) & 1;
+                const int st = it % C::STAGES;
+                const uint32_t ph = (it / C::STAGES) & 1;
+                const int acc = it % MF_NACC;
+                const uint32_t aph = (it / MF_NACC) & 1;
                 if (!mbar_wait(&S->tempty[acc], aph ^ 1, err)) break;
                 tc_fence_after();
                 if (!mbar_wait(&S->full[st], ph, err)) break;
-                const unsigned char* bh = sB + 2 * st * TILE_BYTES;
-                const unsigned char* bl = bh + TILE_BYTES;
-                const uint32_t d = tmem + acc * MF_COLS;
+                tc_fence_after();
+                const unsigned char* ah = sA + 2 * st * TILE;
+                const unsigned char* al = ah + TILE;
+                const uint32_t d = tmem + acc * MF_B;
 #pragma unroll
-                for (int k = 0; k < DPAD / 16; ++k) {
-                    const int kb = k * 32;   // 16 bf16 = 32 bytes along K
-                    umma_bf16(d, smem_desc(sA_hi, SWZ, kb), smem_desc(bh, SWZ, kb), idesc, k > 0 ? 1u : 0u);
-                    umma_bf16(d, smem_desc(sA_hi, SWZ, kb), smem_desc(bl, SWZ, kb), idesc, 1u);
-                    umma_bf16(d, smem_desc(sA_lo, SWZ, kb), smem_desc(bh, SWZ, kb), idesc, 1u);
-                    umma_bf16(d, smem_desc(sA_lo, SWZ, kb), smem_desc(bl, SWZ, kb), idesc, 1u);
+                for (int kk = 0; kk < DPAD / 16; ++kk) {
+                    const int kb = kk * 32;   // 16 bf16 = 32 bytes along K
+                    umma_bf16(d, smem_desc(ah, C::SWZ, kb), smem_desc(sB_hi, C::SWZ, kb), idesc, kk > 0 ? 1u : 0u);
+                    umma_bf16(d, smem_desc(ah, C::SWZ, kb), smem_desc(sB_lo, C::SWZ, kb), idesc, 1u);
+                    umma_bf16(d, smem_desc(al, C::SWZ, kb), smem_desc(sB_hi, C::SWZ, kb), idesc, 1u);
+                    umma_bf16(d, smem_desc(al, C::SWZ, kb), smem_desc(sB_lo, C::SWZ, kb), idesc, 1u);
                 }
                 umma_commit(&S->empty[st]);
                 umma_commit(&S->tfull[acc]);
+                if (++k == mf_row_len(I, sch)) { ++I; k = 0; }
             }
         }
     } else {
-        // ---------------- epilogue: exp and row sums ----------------
-        const int quad = warp & 3, half = warp >> 2;
-        const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-        const int r = quad * 32 + lane;
-        float acc4[4] = {0.f, 0.f, 0.f, 0.f};   // four independent FMA chains
-        int cur_rb = ntiles > 0 ? (int)(t0 / sch.CT) : 0;
-        auto flush = [&](int rb) {   // no barrier: each column half writes its own partial
-            const int slot = g - mf_owner((int64_t)rb * sch.CT, sch);
-            part[(((int64_t)rb * sch.slots + slot) * 2 + half) * MF_ROWS + r] =
-                (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
-            acc4[0] = acc4[1] = acc4[2] = acc4[3] = 0.f;
+        // ---------------- epilogue: exp, row sums and column sums ----------------
+        const int q = warp & 3, h = warp >> 2;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        float2 acc[MF_WCOLS / 2];
+        const float4* pI4 = nullptr;   // p of this warp's 32 columns of block I (L1-resident)
+        int I = I0, k = k0, segI = I0;
+        auto load_seg = [&](int blk) {
+            pI4 = reinterpret_cast<const float4*>(pf + (int64_t)blk * MF_B + h * MF_WCOLS);
+#pragma unroll
+            for (int c = 0; c < MF_WCOLS / 2; ++c) acc[c] = make_float2(0.f, 0.f);
         };
+        auto flush = [&](int blk) {
+            float a[MF_WCOLS];
+#pragma unroll
+            for (int c = 0; c < MF_WCOLS / 2; ++c) { a[2 * c] = acc[c].x; a[2 * c + 1] = acc[c].y; }
+            mf_lane_reduce(a, lane);
+            const int slot = g - mf_owner(mf_row_start(blk, sch), sch);
+            rowpart[(((int64_t)blk * sch.slots + slot) * 4 + q) * MF_B + h * MF_WCOLS + lane] = a[0];
+        };
+        if (ntiles > 0) load_seg(I0);
+        float pj_next = ntiles > 0 ? __ldg(pf + (int64_t)((I0 + k0) % sch.nb) * MF_B + q * 32 + lane) : 0.f;
         for (int it = 0; it < ntiles; ++it) {
-            const int64_t x = t0 + it;
-            const int rb = (int)(x / sch.CT), ct = (int)(x % sch.CT);
-            if (rb != cur_rb) {
-                flush(cur_rb);
-                cur_rb = rb;
+            if (it > 0 && k == 0) {
+                flush(segI);
+                segI = I;
+                load_seg(I);
             }
-            const int acc = it & 1;
-            const uint32_t aph = (it >> 1) & 1;
+            const bool diag = (k == 0);
+            const float pj = pj_next;
+            int In = I, kn = k + 1;
+            if (kn == mf_row_len(I, sch)) { ++In; kn = 0; }
+            if (it + 1 < ntiles) pj_next = __ldg(pf + (int64_t)((In + kn) % sch.nb) * MF_B + q * 32 + lane);
+            const int accb = it % MF_NACC;
+            const uint32_t aph = (it / MF_NACC) & 1;
             // one lane waits, the warp follows: tcgen05.ld below must run converged
-            int ok = (lane == 0) ? (int)mbar_wait(&S->tfull[acc], aph, err) : 0;
+            int ok = (lane == 0) ? (int)mbar_wait(&S->tfull[accb], aph, err) : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            const int jbase = ct * MF_COLS + half * 64;
-#pragma unroll
-            for (int c = 0; c < 64; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + lane_addr + acc * MF_COLS + half * 64 + c, v);
-                const float4* pp = reinterpret_cast<const float4*>(pf + jbase + c);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float4 p4 = __ldg(pp + u);
-                    acc4[0] = fmaf(ex2_approx(v[4 * u + 0]), p4.x, acc4[0]);
-                    acc4[1] = fmaf(ex2_approx(v[4 * u + 1]), p4.y, acc4[1]);
-                    acc4[2] = fmaf(ex2_approx(v[4 * u + 2]), p4.z, acc4[2]);
-                    acc4[3] = fmaf(ex2_approx(v[4 * u + 3]), p4.w, acc4[3]);
-                }
-            }
+            const uint32_t tcol = tmem + lane_addr + accb * MF_B + h * MF_WCOLS;
+            float2 sJ[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            if (diag) mf_tile_epilogue<true>(tcol, acc, pI4, pj, sJ);
+            else mf_tile_epilogue<false>(tcol, acc, pI4, pj, sJ);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S->tempty[acc]);
+            if (lane == 0) mbar_arrive(&S->tempty[accb]);
+            if (!diag)
+                colpart[((t0 + it) * MF_EPW + h) * MF_B + q * 32 + lane] = (sJ[0].x + sJ[0].y) + (sJ[1].x + sJ[1].y);
+            I = In;
+            k = kn;
         }
-        if (ntiles > 0) flush(cur_rb);
+        if (ntiles > 0) flush(segI);
     }
     tc_fence_before();
     __syncthreads();
@@ -359,26 +459,53 @@ __global__ void k_mf_prep(int64_t n, int64_t npad, const double* __restrict__ pi
     pf[i] = (float)p;
 }
 
-// w = lambda p + the row's segment partials (fixed order); p^T w -> delta in the last block.
-__global__ void __launch_bounds__(256)
-k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ part, const double* __restrict__ p,
-            double* __restrict__ w, PcgScalars* sc, double* __restrict__ partials, const int* err) {
+// w_i = lambda p_i + (block row I's segment partials over slots and lane
+// quadrants) + (column sums of the off-diagonal tiles (I', I)).  One CTA per
+// block row I, 4 x 128 threads: group t / 128 takes the distances
+// kk = 1 + group, 5 + group, ...; the groups are added in a fixed order.
+// p^T w -> delta in the last CTA.
+constexpr int MF_FIN_GROUPS = 4;
+__global__ void __launch_bounds__(MF_FIN_GROUPS * MF_B)
+k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ rowpart,
+            const float* __restrict__ colpart, const double* __restrict__ p, double* __restrict__ w, PcgScalars* sc,
+            double* __restrict__ partials, const int* err) {
     if (sc != nullptr && *(volatile const int*)&sc->converged) return;
-    __shared__ double red[8];
-    const int64_t R = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = min(n, (int64_t)blockIdx.x * R), r1 = min(n, r0 + R);
-    double pw = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const int rb = (int)(i / MF_ROWS), r = (int)(i % MF_ROWS);
-        const int64_t x0 = (int64_t)rb * sch.CT;
-        const int g0 = mf_owner(x0, sch), g1 = mf_owner(x0 + sch.CT - 1, sch);
-        double s = 0.0;
+    __shared__ double red[MF_FIN_GROUPS * MF_B / 32];
+    __shared__ float gsum[MF_FIN_GROUPS][MF_B];
+    const int I = blockIdx.x, c = threadIdx.x % MF_B, grp = threadIdx.x / MF_B;
+    float s = 0.f;
+    if (grp == 0) {
+        const int64_t xs = mf_row_start(I, sch);
+        const int g0 = mf_owner(xs, sch), g1 = mf_owner(xs + mf_row_len(I, sch) - 1, sch);
         for (int slot = 0; slot <= g1 - g0; ++slot)
-            for (int h = 0; h < 2; ++h)
-                s += (double)part[(((int64_t)rb * sch.slots + slot) * 2 + h) * MF_ROWS + r];
-        const double wi = fma(lambda, p[i], s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s += rowpart[(((int64_t)I * sch.slots + slot) * 4 + q) * MF_B + c];
+    }
+    float t[2] = {0.f, 0.f};
+    int u = 0;
+    for (int kk = 1 + grp; kk <= sch.base; kk += MF_FIN_GROUPS, u ^= 1) {
+        int Ip = I - kk;
+        if (Ip < 0) Ip += sch.nb;
+        if (kk < mf_row_len(Ip, sch)) {
+            const int64_t x = mf_row_start(Ip, sch) + kk;
+            const float* cp = colpart + x * MF_EPW * MF_B + c;
+            float v = 0.f;
+#pragma unroll
+            for (int h = 0; h < MF_EPW; ++h) v += cp[h * MF_B];
+            t[u] += v;
+        }
+    }
+    gsum[grp][c] = s + (t[0] + t[1]);
+    __syncthreads();
+    const int64_t i = (int64_t)I * MF_B + c;
+    double pw = 0.0;
+    if (grp == 0 && i < n) {
+        double tot = 0.0;
+#pragma unroll
+        for (int gq = 0; gq < MF_FIN_GROUPS; ++gq) tot += (double)gsum[gq][c];
+        const double wi = fma(lambda, p[i], tot);
         w[i] = wi;
-        pw = fma(p[i], wi, pw);
+        pw = p[i] * wi;
     }
     if (sc == nullptr) return;
     pw = lk::block_sum(pw, red);
@@ -413,11 +540,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode(laker_ctx* ctx) {
     return fn;
 }
 
-// Dynamic shared memory per CTA; at least 80 KB so that at most two CTAs
-// share an SM and their 2 x 256 tensor-memory columns never wait in alloc.
+// Dynamic shared memory per CTA; at least 120 KB so that one CTA holds an SM
+// and its 512 tensor-memory columns never wait in alloc.
 size_t mf_smem_bytes(int dpad) {
-    const size_t tile = (size_t)MF_ROWS * dpad * 2;
-    return std::max<size_t>(80 * 1024, 1024 + (2 + 2 * MF_STAGES) * tile + sizeof(MfSmem));
+    const size_t tile = (size_t)MF_B * dpad * 2;
+    const int stages = dpad >= 64 ? MfCfg<64>::STAGES : MfCfg<32>::STAGES;
+    return std::max<size_t>(120 * 1024, 1024 + (2 + 2 * (size_t)stages) * tile + sizeof(MfSmem));
 }
 
 }  // namespace
@@ -425,12 +553,32 @@ size_t mf_smem_bytes(int dpad) {
 // Workspace of the matrix-free operator, allocated at build time.
 struct MfWork {
     CUtensorMap map_hi, map_lo;
-    float* pf = nullptr;       // padded float32 p
-    float* part = nullptr;     // segment partial row sums (see MfSched)
-    int* err = nullptr;        // device error word
+    float* pf = nullptr;        // padded float32 p
+    float* rowpart = nullptr;   // segment row sums (see k_mf_bf16x3)
+    float* colpart = nullptr;   // column sums of off-diagonal tiles
+    int* err = nullptr;         // device error word
     MfSched sch;
-    int col_tiles = 0;
 };
+
+static void mf_release_work(MfWork* wk);
+
+namespace {
+
+laker_status mf_launch_main(laker_ctx* ctx, const laker_op* op, const MfWork* wk, const PcgScalars* sc) {
+    const size_t smem = mf_smem_bytes(op->dpad);
+    const unsigned grid = (unsigned)wk->sch.G;
+#define LK_MF_LAUNCH(D)                                                                                        \
+    k_mf_bf16x3<D><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch, wk->rowpart, \
+                                                             wk->colpart, wk->err, sc)
+    if (op->dpad == 16) LK_MF_LAUNCH(16);
+    else if (op->dpad == 32) LK_MF_LAUNCH(32);
+    else LK_MF_LAUNCH(64);
+#undef LK_MF_LAUNCH
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}
+
+}  // namespace
 
 laker_status mf_prepare(laker_ctx* ctx, laker_op* op) {
     if (!(op->dpad == 16 || op->dpad == 32 || op->dpad == 64))
@@ -439,27 +587,31 @@ laker_status mf_prepare(laker_ctx* ctx, laker_op* op) {
     if (!encode) return LAKER_ERR_CUDA;
     MfWork* wk = new MfWork();
     const int64_t n = op->n;
-    const int64_t npad = (n + MF_COLS - 1) / MF_COLS * MF_COLS;
-    wk->col_tiles = (int)(npad / MF_COLS);
-    const int row_blocks = (int)((n + MF_ROWS - 1) / MF_ROWS);
     MfSched& sc = wk->sch;
-    sc.CT = wk->col_tiles;
-    sc.T = (int64_t)row_blocks * sc.CT;
-    sc.G = (int)std::min<int64_t>(sc.T, 2 * (int64_t)ctx->num_sms);
+    sc.nb = (int)((n + MF_B - 1) / MF_B);
+    sc.base = (sc.nb - 1) / 2 + 1;
+    sc.half = (sc.nb % 2 == 0) ? sc.nb / 2 : 0;
+    sc.T = (int64_t)sc.half * (sc.base + 1) + (int64_t)(sc.nb - sc.half) * sc.base;
+    sc.G = (int)std::min<int64_t>(sc.T, (int64_t)ctx->num_sms);
     sc.slots = 1;
-    for (int rb = 0; rb < row_blocks; ++rb) {
-        const int64_t x0 = (int64_t)rb * sc.CT;
-        sc.slots = std::max(sc.slots, mf_owner(x0 + sc.CT - 1, sc) - mf_owner(x0, sc) + 1);
+    for (int I = 0; I < sc.nb; ++I) {
+        const int64_t x0 = mf_row_start(I, sc);
+        sc.slots = std::max(sc.slots, mf_owner(x0 + mf_row_len(I, sc) - 1, sc) - mf_owner(x0, sc) + 1);
     }
+    const int64_t npad = (int64_t)sc.nb * MF_B;
     laker_status st;
     if ((st = lk_malloc(ctx, (void**)&wk->pf, (size_t)npad * sizeof(float))) != LAKER_OK) { delete wk; return st; }
-    if ((st = lk_malloc(ctx, (void**)&wk->part, (size_t)row_blocks * sc.slots * 2 * MF_ROWS * sizeof(float))) !=
-        LAKER_OK) { delete wk; return st; }
-    if ((st = lk_malloc(ctx, (void**)&wk->err, sizeof(int))) != LAKER_OK) { delete wk; return st; }
+    if ((st = lk_malloc(ctx, (void**)&wk->rowpart, (size_t)sc.nb * sc.slots * 4 * MF_B * sizeof(float))) !=
+        LAKER_OK) { mf_release_work(wk); return st; }
+    if ((st = lk_malloc(ctx, (void**)&wk->colpart, (size_t)sc.T * MF_EPW * MF_B * sizeof(float))) != LAKER_OK) {
+        mf_release_work(wk);
+        return st;
+    }
+    if ((st = lk_malloc(ctx, (void**)&wk->err, sizeof(int))) != LAKER_OK) { mf_release_work(wk); return st; }
     LK_CUDA(ctx, cudaMemsetAsync(wk->err, 0, sizeof(int), ctx->stream));
     const cuuint64_t dims[2] = {(cuuint64_t)op->dpad, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)op->dpad * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)op->dpad, (cuuint32_t)MF_ROWS};
+    const cuuint32_t box[2] = {(cuuint32_t)op->dpad, (cuuint32_t)MF_B};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapSwizzle swz = op->dpad == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
                                    : op->dpad == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
@@ -469,25 +621,32 @@ laker_status mf_prepare(laker_ctx* ctx, laker_op* op) {
                             which == 0 ? (void*)op->Qhi : (void*)op->Qlo, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) { delete wk; return set_error(ctx, LAKER_ERR_CUDA, "cuTensorMapEncodeTiled failed"); }
+        if (r != CUDA_SUCCESS) {
+            mf_release_work(wk);
+            return set_error(ctx, LAKER_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        }
     }
     const size_t smem = mf_smem_bytes(op->dpad);
     cudaError_t e;
     if (op->dpad == 16) e = cudaFuncSetAttribute(k_mf_bf16x3<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else if (op->dpad == 32) e = cudaFuncSetAttribute(k_mf_bf16x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else e = cudaFuncSetAttribute(k_mf_bf16x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) { delete wk; return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    if (e != cudaSuccess) { mf_release_work(wk); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
     op->mf = wk;
     return LAKER_OK;
 }
 
-void mf_release(laker_op* op) {
-    MfWork* wk = static_cast<MfWork*>(op->mf);
+static void mf_release_work(MfWork* wk) {
     if (!wk) return;
     cudaFree(wk->pf);
-    cudaFree(wk->part);
+    cudaFree(wk->rowpart);
+    cudaFree(wk->colpart);
     cudaFree(wk->err);
     delete wk;
+}
+
+void mf_release(laker_op* op) {
+    mf_release_work(static_cast<MfWork*>(op->mf));
     op->mf = nullptr;
 }
 
@@ -505,24 +664,14 @@ laker_status mf_matvec_launch(laker_ctx* ctx, const laker_op* op, const double* 
     const MfWork* wk = static_cast<const MfWork*>(op->mf);
     if (!wk) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "matrix-free operator not prepared");
     const int64_t n = op->n;
-    const int64_t npad = (int64_t)wk->col_tiles * MF_COLS;
+    const int64_t npad = (int64_t)wk->sch.nb * MF_B;
     const double* p = fuse ? pout : pin;
     k_mf_prep<<<(unsigned)((npad + 255) / 256), 256, 0, ctx->stream>>>(n, npad, pin, z, pout, wk->pf, sc, fuse);
     LK_LAUNCHED(ctx);
-    const size_t smem = mf_smem_bytes(op->dpad);
-    const unsigned grid = (unsigned)wk->sch.G;
-    if (op->dpad == 16)
-        k_mf_bf16x3<16><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch, wk->part,
-                                                                 wk->err, sc);
-    else if (op->dpad == 32)
-        k_mf_bf16x3<32><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch, wk->part,
-                                                                 wk->err, sc);
-    else
-        k_mf_bf16x3<64><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch, wk->part,
-                                                                 wk->err, sc);
-    LK_LAUNCHED(ctx);
-    const int fb = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 2 * ctx->num_sms);
-    k_mf_finish<<<fb, 256, 0, ctx->stream>>>(n, wk->sch, op->lambda, wk->part, p, w, sc, partials, wk->err);
+    laker_status st = mf_launch_main(ctx, op, wk, sc);
+    if (st != LAKER_OK) return st;
+    k_mf_finish<<<wk->sch.nb, MF_FIN_GROUPS * MF_B, 0, ctx->stream>>>(n, wk->sch, op->lambda, wk->rowpart, wk->colpart, p, w, sc, partials,
+                                             wk->err);
     LK_LAUNCHED(ctx);
     return LAKER_OK;
 }
@@ -531,34 +680,25 @@ laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, i
     const MfWork* wk = static_cast<const MfWork*>(op->mf);
     if (!wk) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "matrix-free operator not prepared");
     const int64_t n = op->n;
-    const int64_t npad = (int64_t)wk->col_tiles * MF_COLS;
+    const int64_t npad = (int64_t)wk->sch.nb * MF_B;
     k_mf_prep<<<(unsigned)((npad + 255) / 256), 256, 0, ctx->stream>>>(n, npad, x, nullptr, nullptr, wk->pf, nullptr,
                                                                        0);
     LK_LAUNCHED(ctx);
-    const size_t smem = mf_smem_bytes(op->dpad);
-    const unsigned grid = (unsigned)wk->sch.G;
     cudaEvent_t e0, e1;
     LK_CUDA(ctx, cudaEventCreate(&e0));
     LK_CUDA(ctx, cudaEventCreate(&e1));
-    for (int rep = -1; rep < reps; ++rep) {
+    laker_status st = LAKER_OK;
+    for (int rep = -1; rep < reps && st == LAKER_OK; ++rep) {
         if (rep == 0) LK_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-        if (op->dpad == 16)
-            k_mf_bf16x3<16><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch,
-                                                                     wk->part, wk->err, nullptr);
-        else if (op->dpad == 32)
-            k_mf_bf16x3<32><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch,
-                                                                     wk->part, wk->err, nullptr);
-        else
-            k_mf_bf16x3<64><<<grid, MF_THREADS, smem, ctx->stream>>>(wk->map_hi, wk->map_lo, wk->pf, wk->sch,
-                                                                     wk->part, wk->err, nullptr);
-        LK_LAUNCHED(ctx);
+        st = mf_launch_main(ctx, op, wk, nullptr);
     }
-    LK_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-    LK_CUDA(ctx, cudaEventSynchronize(e1));
+    if (st == LAKER_OK) LK_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    if (st == LAKER_OK) LK_CUDA(ctx, cudaEventSynchronize(e1));
     float t = 0.f;
-    LK_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
+    if (st == LAKER_OK) LK_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st != LAKER_OK) return st;
     *ms = (double)t / reps;
     return mf_status(ctx, op);
 }

@@ -582,7 +582,8 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
     if ((st = lk_malloc(ctx, (void**)&base, (size_t)6 * n * sizeof(double))) != LAKER_OK) return st;
     ws.r = base; ws.z = base + n; ws.p[0] = base + 2 * n; ws.p[1] = base + 3 * n; ws.w = base + 4 * n;
     ws.w2 = base + 5 * n;
-    const int nb = 4 * ctx->num_sms + 8;   // per-block partials of any of the kernels
+    // per-block partials of any of the kernels (the matrix-free finish runs one block per 128 rows)
+    const int64_t nb = std::max<int64_t>(4 * ctx->num_sms + 8, (n + 127) / 128 + 8);
     if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
     const int nr = std::max(1, n_r);
     if ((st = lk_malloc(ctx, &ws.t, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
