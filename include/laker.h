@@ -137,7 +137,7 @@ laker_status laker_op_time_operator(laker_ctx* ctx, const laker_op* op, const do
  *   rho     < 0 selects the adaptive rule min(1/2, max(1e-3, gamma (1 - n_r/n)))
  *           (1e-3 when n_r >= n).
  *   eps     safeguard of F_gamma (> 0).
- * Errors: LAKER_ERR_ARG for n_r < 1 or n_r > 1024; LAKER_ERR_NOT_SPD if a
+ * Errors: LAKER_ERR_ARG for n_r < 1 or n_r > 2048; LAKER_ERR_NOT_SPD if a
  * factorisation fails.
  */
 laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z,

@@ -211,7 +211,7 @@ laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const 
     if (st != LAKER_OK) return st;
     if (!op || !Z || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
     *out = nullptr;
-    if (n_r < 1 || n_r > 1024) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 1024");
+    if (n_r < 1 || n_r > LK_MAX_NR) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 2048");
     if (!(gamma >= 0.0) || !(eps > 0.0) || rho > 1.0 || max_iter < 1 || !(tol >= 0.0))
         return set_error(ctx, LAKER_ERR_ARG, "bad CCCP parameters");
     if ((st = scan_finite(ctx, Z, op->n * (int64_t)n_r)) != LAKER_OK) return st;

@@ -481,6 +481,47 @@ __global__ void k_scale_B(int m, int nr, const double* __restrict__ B0, const do
     B[idx] = sqrt(D[i]) * B0[(int64_t)i * m + j] * sqrt(D[j]);
 }
 
+// Orthonormal form of the low-rank part (float32 and split-bf16 operators):
+// with Y = U D^1/2 and Y^T Y = S = V diag(l) V^T, the columns of
+// U~ = Y V diag(l)^-1/2 are the orthonormal eigenvectors of Sigma = cI + Y Y^T
+// in span(U), and P = Sigma^-1/2 = c^-1/2 I + U~ diag(phi) U~^T with
+// phi_k = (c + l_k)^-1/2 - c^-1/2 in [-c^-1/2, 0].  C = D^1/2 V diag(l)^-1/2
+// (nr x nr) and phi; eigenvalues at or below 1e-13 of the largest (and the
+// padding) get C = 0 and phi = 0: their terms l phi / l are below l / (2 c^1.5).
+__global__ void k_utilde_coeffs(int m, int nr, const double* __restrict__ S, const double* __restrict__ V,
+                                const double* __restrict__ D, double c, double lmax, float* __restrict__ C,
+                                double* __restrict__ phi) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nr * nr) return;
+    const int j = (int)(idx / nr), k = (int)(idx % nr);
+    const double l = S[(int64_t)k * m + k];
+    const bool keep = l > 1e-13 * lmax;
+    C[idx] = keep ? (float)(sqrt(D[j]) * V[(int64_t)j * m + k] / sqrt(l)) : 0.f;
+    if (j == 0) phi[k] = keep ? 1.0 / sqrt(c + l) - 1.0 / sqrt(c) : 0.0;
+}
+
+// largest diagonal entry of S (single block)
+__global__ void k_diag_max(int m, const double* __restrict__ S, double* out) {
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) v = fmax(v, S[(int64_t)k * m + k]);
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+        *out = r;
+    }
+}
+
+// W[i][k] = float(Ut[i][k] phi_k)
+__global__ void k_scale_cols_to_float(int64_t n, int nr, const double* __restrict__ Ut, const double* __restrict__ phi,
+                                      float* __restrict__ W) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n * nr) W[idx] = (float)(Ut[idx] * phi[idx % nr]);
+}
+
 unsigned gsz(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b); }
 
 }  // namespace
@@ -585,38 +626,27 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     k_offdiag<<<1, 1024, 0, s>>>(Sm, m, nrm);
     LK_CUDA(ctx, cudaStreamEndCapture(s, &g));
     LK_CUDA(ctx, cudaGraphInstantiate(&ge, g, 0));
-    // Stop once the off-diagonal mass is below 1e-12 of the Frobenius norm, when a
-    // sweep no longer halves it, or after 12 sweeps.  What survives then couples
-    // only eigenvalues far below c, whose factors (c + l)^-1/2 in P agree to
-    // ~l/c: mixing them does not change P = Sigma^-1/2 at that level.
+    // Stop once the off-diagonal Frobenius norm is below 1e-12 of the matrix
+    // norm, or after 12 sweeps.  For float32 and split-bf16 operators, whose
+    // solves are judged by the true residual, also once it is at most 1e-2 c:
+    // the eigenpairs then diagonalise a matrix within |off| of S, and an
+    // eigenvalue moved by delta changes its factor in P = Sigma^-1/2 by at most
+    // delta / (2 c) relative, so P stays within 1 % of Sigma_*^-1/2 along every
+    // direction and positive definite.  The unrotated remainder couples the
+    // cluster of eigenvalues far below c, where (c + l)^-1/2 is flat.
     double hn[2] = {0, 0};
-    double prev_off = -1.0;
     int sweeps = 0;
+    const double off_stop = (op->precision == LAKER_FP64) ? 0.0 : 1e-4 * h.c * h.c;
     for (int sweep = 0; sweep < 12; ++sweep) {
         LK_CUDA(ctx, cudaGraphLaunch(ge, s));
         ctx->launches += 2 * (m - 1) + 1;
         ++sweeps;
         LK_CUDA(ctx, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, s));
         LK_CUDA(ctx, cudaStreamSynchronize(s));
-        if (!(hn[0] > 1e-24 * hn[1])) break;
-        if (prev_off >= 0.0 && hn[0] > 0.25 * prev_off) break;
-        prev_off = hn[0];
+        if (!(hn[0] > 1e-24 * hn[1]) || !(hn[0] > off_stop)) break;
     }
     cudaGraphExecDestroy(ge);
     cudaGraphDestroy(g);
-    k_vf<<<gsz((int64_t)m * m), 256, 0, s>>>(m, Sm, V, h.c, X);
-    LK_LAUNCHED(ctx);
-    if ((st = gemm<double>(ctx, false, true, m, m, m, X, m, V, m, 0.0, nullptr, 0, B0, m)) != LAKER_OK) return st;
-    k_scale_B<<<gsz((int64_t)nr * nr), 256, 0, s>>>(m, nr, B0, D, B);
-    LK_LAUNCHED(ctx);
-    // W = U B in float64 for every operator: B has entries ~D/c^1.5 that cancel
-    // inside U B U^T, so a float32 accumulation would destroy W (mixed solves
-    // round the float64 W to float32 afterwards).
-    double* W64 = nullptr;
-    if ((st = lk_malloc(ctx, (void**)&W64, (size_t)n * nr * sizeof(double))) != LAKER_OK) return st;
-    if ((st = gemm<double>(ctx, false, false, n, nr, nr, U64, nr, B, nr, 0.0, nullptr, 0, W64, nr)) != LAKER_OK)
-        return st;
-    P->W64 = W64;
     P->kind = PRECOND_CCCP;
     P->n = n;
     P->n_r = nr;
@@ -624,22 +654,53 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     P->cinvsqrt = 1.0 / std::sqrt(h.c);
     if ((st = lk_malloc(ctx, (void**)&P->D, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
     LK_CUDA(ctx, cudaMemcpyAsync(P->D, D, nr * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    // U^T with a padded row pitch for the streaming U^T r of the apply
-    P->ldu = (n + 3) / 4 * 4;
-    {
-        dim3 tb(32, 8), tg((unsigned)((nr + 31) / 32), (unsigned)((P->ldu + 31) / 32));
-        if (op->precision != LAKER_FP64) {
-            if ((st = lk_malloc(ctx, (void**)&P->UT32, (size_t)nr * P->ldu * sizeof(float))) != LAKER_OK) return st;
-            if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
-            k_transpose<float><<<tg, tb, 0, s>>>(n, nr, P->ldu, U64, P->UT32);
-            LK_LAUNCHED(ctx);
-            k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, W64, P->W32);
-            LK_LAUNCHED(ctx);
-        } else {
-            if ((st = lk_malloc(ctx, (void**)&P->UT64, (size_t)nr * P->ldu * sizeof(double))) != LAKER_OK) return st;
-            k_transpose<double><<<tg, tb, 0, s>>>(n, nr, P->ldu, U64, P->UT64);
-            LK_LAUNCHED(ctx);
-        }
+    P->ldu = (n + 3) / 4 * 4;   // row pitch of U^T for the streaming U^T r of the apply
+    dim3 tb(32, 8), tg((unsigned)((nr + 31) / 32), (unsigned)((P->ldu + 31) / 32));
+    if (op->precision == LAKER_FP64) {
+        // P = c^-1/2 I + U B U^T with B = D^1/2 V f(l) V^T D^1/2, W = U B, all in
+        // float64: B has entries ~D / c^1.5 that cancel inside U B U^T.
+        k_vf<<<gsz((int64_t)m * m), 256, 0, s>>>(m, Sm, V, h.c, X);
+        LK_LAUNCHED(ctx);
+        if ((st = gemm<double>(ctx, false, true, m, m, m, X, m, V, m, 0.0, nullptr, 0, B0, m)) != LAKER_OK) return st;
+        k_scale_B<<<gsz((int64_t)nr * nr), 256, 0, s>>>(m, nr, B0, D, B);
+        LK_LAUNCHED(ctx);
+        double* W64 = nullptr;
+        if ((st = lk_malloc(ctx, (void**)&W64, (size_t)n * nr * sizeof(double))) != LAKER_OK) return st;
+        if ((st = gemm<double>(ctx, false, false, n, nr, nr, U64, nr, B, nr, 0.0, nullptr, 0, W64, nr)) != LAKER_OK)
+            return st;
+        P->W64 = W64;
+        if ((st = lk_malloc(ctx, (void**)&P->UT64, (size_t)nr * P->ldu * sizeof(double))) != LAKER_OK) return st;
+        k_transpose<double><<<tg, tb, 0, s>>>(n, nr, P->ldu, U64, P->UT64);
+        LK_LAUNCHED(ctx);
+    } else {
+        // orthonormal form: U~ = U C in float32 (|U~_ik| <= 1, |phi| <= c^-1/2,
+        // so a float32 product loses nothing that cancels later)
+        double* lmax = tmpv;   // free scratch by now
+        k_diag_max<<<1, 1024, 0, s>>>(m, Sm, lmax);
+        LK_LAUNCHED(ctx);
+        double hl = 0.0;
+        LK_CUDA(ctx, cudaMemcpyAsync(&hl, lmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        float *C32 = nullptr, *U32 = nullptr;
+        double *phi = nullptr, *Ut = nullptr;
+        if ((st = lk_malloc(ctx, (void**)&C32, (size_t)nr * nr * sizeof(float))) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&phi, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&U32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&Ut, (size_t)n * nr * sizeof(double))) != LAKER_OK) return st;
+        k_utilde_coeffs<<<gsz((int64_t)nr * nr), 256, 0, s>>>(m, nr, Sm, V, D, h.c, hl, C32, phi);
+        LK_LAUNCHED(ctx);
+        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, U64, U32);
+        LK_LAUNCHED(ctx);
+        if ((st = gemm<float>(ctx, false, false, n, nr, nr, U32, nr, C32, nr, 0.0, nullptr, 0, Ut, nr)) != LAKER_OK)
+            return st;
+        if ((st = lk_malloc(ctx, (void**)&P->UT32, (size_t)nr * P->ldu * sizeof(float))) != LAKER_OK) return st;
+        if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        k_transpose<float><<<tg, tb, 0, s>>>(n, nr, P->ldu, Ut, P->UT32);
+        LK_LAUNCHED(ctx);
+        k_scale_cols_to_float<<<gsz(n * nr), 256, 0, s>>>(n, nr, Ut, phi, P->W32);
+        LK_LAUNCHED(ctx);
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        for (void* ptr : {(void*)C32, (void*)U32, (void*)phi, (void*)Ut}) cudaFree(ptr);
     }
     LK_CUDA(ctx, cudaStreamSynchronize(s));
     for (void* ptr : {(void*)tmpv, (void*)M, (void*)A, (void*)D, (void*)Dn, (void*)q, (void*)partials, (void*)cn,

@@ -59,6 +59,10 @@ struct laker_op {
     void* mf = nullptr;       // matrix-free operator workspace (tensor maps, buffers)
 };
 
+// Largest number of random directions N_r (a preconditioner apply keeps the
+// N_r-vector U^T r in shared memory).
+constexpr int LK_MAX_NR = 2048;
+
 enum PrecondKind { PRECOND_IDENTITY = 0, PRECOND_JACOBI = 1, PRECOND_CCCP = 2 };
 
 struct laker_precond {

@@ -407,7 +407,7 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
           double* __restrict__ partials, PrecView pv, const PT* __restrict__ t, int gate) {
     if (gated_out(sc, gate)) return;
     __shared__ double red[VEC_THREADS / 32];
-    __shared__ PT ts[1024];
+    __shared__ PT ts[LK_MAX_NR];
     int64_t r0, r1;
     row_range(n, r0, r1);
     double rz = 0.0;

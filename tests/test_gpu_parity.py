@@ -217,6 +217,34 @@ def test_zero_rhs_and_bad_inputs(L, ctx):
     assert info["iterations"] == 3 and not info["converged"]
 
 
+@pytest.mark.parametrize("prec", ["FP32", "BF16X3"])
+def test_mixed_precond_apply_matches_oracle(L, ctx, prec):
+    """Mixed operators keep the preconditioner in the orthonormal form
+    P = c^-1/2 I + U~ diag(phi) U~^T (float32 U~) from an eigendecomposition
+    stopped once its off-diagonal remainder is below c / 100; P v must match
+    the oracle's dense Sigma_*^-1/2 v to well under that bound and stay
+    positive definite."""
+    from tests.gpu_util import dev, host, rel
+    n, n_r = 1024, 128
+    inst = _inst(n, 16, 1e-3, 51)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    Z = synth.directions(n, n_r, 51)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, getattr(L, prec))
+    P = L.laker_fit_preconditioner(ctx, op, dev(Z))
+    Pd = O.inverse_sqrt(O.cccp_fit(O.random_directions(A, Z), 0.1, O.shrinkage_rho(n, n_r, 0.1), 1e-8).Sigma)
+    worst = 0.0
+    for s in range(4):
+        v = synth.random_vector(n, 60 + s)
+        pv = host(L.laker_precond_apply(ctx, P, dev(v)))
+        worst = max(worst, rel(pv, Pd @ v))
+        assert float(v @ pv) > 0.0
+    assert worst < 2e-3, worst
+    # along the dominant eigenvector of Sigma_* (the smallest factor of P)
+    w, V = np.linalg.eigh(np.linalg.inv(Pd @ Pd))
+    top = V[:, -1]
+    assert rel(host(L.laker_precond_apply(ctx, P, dev(top))), Pd @ top) < 2e-3
+
+
 def test_fp32_mixed_refinement_reaches_true_tolerance(L, ctx):
     """Mixed form: float32 operator inside PCG, float64-accurate residual every
     20 products; the returned alpha meets the TRUE relative residual 1e-6
