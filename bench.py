@@ -37,6 +37,11 @@ METRIC = "PCG solves/s at rel-res 1e-6 (mixed)"
 UNIT = "solves/s"
 CFG = dict(n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6, refine_every=20)
 SEED = 2000
+# DRAM bytes (read + write) of one k_mf_bf16x3 launch at this workload, from the
+# ncu capture summarised in profiles/k_mf_bf16x3_n16384_d32.md (None until a
+# capture of the current kernel exists); the operands Q_hi, Q_lo are read from
+# DRAM once, everything else stays in L2.
+MF_TRAFFIC_BYTES = 2205696
 
 
 def workload(seed: int):
@@ -205,16 +210,19 @@ def run_ours(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    # roofline of the dominant kernel: the tcgen05 matrix-free operator.  Per pair
-    # it executes 4 split-bf16 products of 2 * dpad flops on the tensor pipe and
-    # one ex2 on the MUFU pipe; the binding roof is the larger of the two times.
+    # roofline of the dominant kernel: the tcgen05 matrix-free operator.  It
+    # computes each unordered pair of points once (n(n+1)/2 pairs, as 128 x 128
+    # tiles of the block pairs I <= J): per pair 4 split-bf16 products of
+    # 2 * dpad flops on the tensor pipe and one ex2 on the MUFU pipe; the
+    # binding roof is the larger of the two times.
     op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.BF16X3)
     x = to_dev(synth.random_vector(inst.n, 1))
     mv_ms = L.laker_op_time_operator(ctx, op, x, reps=30)
     op.close()
     n = inst.n
     dpad = (inst.d + 15) // 16 * 16
-    pairs = float(n) * n
+    nb = (n + 127) // 128
+    pairs = float(nb * (nb + 1) // 2) * 128 * 128
     flops = pairs * 4 * 2 * dpad
     bf16_peak, peak_kind = peaks_bf16()
     sfu_peak = 32 * 152 * 2.07e9                     # ex2/s: 32 per clock per SM (measured) x SMs x max clock
@@ -264,9 +272,9 @@ def run_ours(args):
         "plain_fp64": plain,
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, row sums)", "bound": "tensor",
+        "roofline": {"kernel": "k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, row and column sums)", "bound": "tensor",
                      "achieved": achieved, "peak": bf16_peak, "peak_kind": peak_kind + " bf16 burst",
-                     "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": MF_TRAFFIC_BYTES,
                      "flops_per_launch": flops, "ms_per_launch": mv_ms,
                      "tensor_bound_ms": t_tensor * 1e3, "sfu_bound_ms": t_sfu * 1e3,
                      "frac_of_binding_roof": max(t_tensor, t_sfu) * 1e3 / mv_ms},
