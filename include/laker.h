@@ -171,6 +171,42 @@ laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_pre
                              const double* y, double* alpha, double tol, int max_iter,
                              int refine_every, laker_solve_info* info);
 
+/* One instance of a batched solve: its operator, preconditioner (NULL =
+ * identity), right-hand side y (device, n) and output alpha (device, n). */
+typedef struct {
+    const laker_op* op;
+    const laker_precond* P;
+    const double* y;
+    double* alpha;
+} laker_batch_item;
+
+/*
+ * Batched PCG (the PCG stage of Algorithm 1, Sec. IV-E, for `count`
+ * independent instances of any sizes) in one persistent cooperative launch.
+ * Each instance runs the iteration of laker_pcg_solve with its own float64
+ * scalars and stops on its own test; instances that stop leave the shared
+ * work lists.
+ *   items      host array of `count` instances.  Operators must be
+ *              materialised and share a precision class: all FP64, or all
+ *              FP32 / BF16X3 (these use the float32 G for the product and the
+ *              float32 pair for the float64-accurate true residual).  CCCP
+ *              preconditioners must come from operators of the same class.
+ *   refine_every  as in laker_pcg_solve (mixed instances).
+ *   infos      host array of `count` (may be NULL); rel_res_true is the
+ *              float64-accurate residual of the returned alpha.
+ *   done_ms    host array of `count` (may be NULL): time from the launch
+ *              start to each instance's stop, from the device clock.
+ * The first call for a batch shape (count, total n) times six candidate work
+ * shapes (rows per work item x CTAs per SM) on 8 products each and keeps the
+ * fastest.  The call allocates its workspace and synchronises the stream.
+ * Errors: LAKER_ERR_ARG / LAKER_ERR_UNSUPPORTED for mixed precision classes or
+ * non-materialised operators; LAKER_ERR_BREAKDOWN or LAKER_ERR_MAXITER if any
+ * instance failed (its info says which; every alpha is written).
+ */
+laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items,
+                                     double tol, int max_iter, int refine_every,
+                                     laker_solve_info* infos, double* done_ms);
+
 /*
  * Radio-map reconstruction (Sec. III-A, Eq. sc-radio-map-reconstruction;
  * Algorithm 1, reconstruction stage):  out_m = sum_i exp(scale <qg_m, q_i>) alpha_i.

@@ -282,6 +282,19 @@ laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_pre
     return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info);
 }
 
+laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items, double tol,
+                                     int max_iter, int refine_every, laker_solve_info* infos, double* done_ms) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (count < 1 || !items) return set_error(ctx, LAKER_ERR_ARG, "need count >= 1 and items");
+    if (!(tol >= 0.0) || max_iter < 1 || refine_every < 0) return set_error(ctx, LAKER_ERR_ARG, "bad PCG parameters");
+    for (int i = 0; i < count; ++i) {
+        if (!items[i].op || !items[i].y || !items[i].alpha) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+        if ((st = scan_finite(ctx, items[i].y, items[i].op->n)) != LAKER_OK) return st;
+    }
+    return pcg_solve_batched(ctx, count, items, tol, max_iter, refine_every, infos, done_ms);
+}
+
 laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
                             double* out) {
     laker_status st = check_ctx(ctx);

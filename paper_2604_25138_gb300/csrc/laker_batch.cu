@@ -1,0 +1,674 @@
+// Batched PCG: many independent instances (Algorithm 1, PCG stage, once per
+// instance) solved together in ONE persistent cooperative launch.
+//
+// Data written by one CTA and read by another inside the launch is read with
+// ld.global.cg (L2), so no SM's L1 copy can be stale across a barrier.
+//
+// Every phase of an iteration -- operator product (materialised G), step
+// length, update of alpha and r, stop test, true residual, U^T r, W t,
+// beta, new direction -- is a grid-stride loop over a global work list of
+// (instance, block of R rows) or (instance, block of directions) items,
+// followed by a bounded grid barrier.  Converged instances drop out of every
+// work list, so the grid always works on the instances still running.  The
+// per-instance scalars are float64; each reduction sums per-item partials in
+// a fixed order (deterministic).  Mixed instances (float32 G) replace r by
+// y - (lambda I + G) alpha computed in float64 from the float32 pair every
+// `refine_every` products and whenever the recursive residual passes, as the
+// single-instance solver does.
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "laker_device.cuh"
+
+namespace {
+
+constexpr int BT = 256;                 // threads per CTA
+constexpr int BW = BT / 32;             // warps per CTA
+
+struct BInst {
+    int64_t n, ldk;
+    double lambda;
+    const float* K32;      // mixed: G rounded to float32 (n x ldk)
+    const float* K32lo;    // mixed: G - K32 in float32
+    const double* K64;     // float64 instances
+    int kind;              // PRECOND_*
+    int n_r;
+    int64_t ldu;
+    double cinv;
+    const void* UT;        // n_r x ldu
+    const void* W;         // n x n_r
+    const double* dinv;
+    const double* y;
+    double* alpha;
+    double *r, *z, *p, *w;
+    float* pf;             // float32 copy of p, zero-padded to ldk (mixed)
+    double* t;             // U^T r (n_r)
+    int64_t row0;          // first row item
+    int rows;              // row items
+    int64_t kit0;          // first direction item
+    int kits;              // direction items
+};
+
+struct BScal {
+    double rz, pAp, delta, beta, rr, yy, tol2yy, rr_true;
+    int converged;         // 0 running, 1 converged, 2 breakdown / non-finite, 3 max_iter
+    int iters, need_true, true_count;
+    unsigned long long t_done;   // %globaltimer at exit (ns)
+};
+
+struct BGlobal {
+    lk::GridSync gs;
+    int err;
+    int active[2];         // running instances, by iteration parity
+    int need_true[2];      // instances due for a true residual, by parity
+    unsigned long long t0;
+};
+
+struct BArgs {
+    int count;
+    const BInst* inst;
+    BScal* sc;
+    const int* row_inst;   // row item -> instance
+    int64_t row_items;
+    const int* k_inst;     // direction item -> instance
+    int64_t k_items;
+    int R;                 // rows per row item
+    double* part;          // one partial per row item / direction item
+    BGlobal* g;
+    int max_iter;
+    int refine_every;
+    int mixed;             // 1: float32 product + float64-accurate true residual
+};
+
+constexpr int KB = BW;     // directions per direction item (one per warp)
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool running(const BArgs& a, int i) {
+    return *(volatile const int*)&a.sc[i].converged == 0;
+}
+
+__device__ __forceinline__ void finish(BScal& s, int code) {
+    s.converged = code;
+    s.t_done = globaltimer();
+}
+
+// Fixed-order sum of the per-item partials [p0, p0 + cnt) (one thread).
+__device__ __forceinline__ double sum_items(const double* part, int64_t p0, int cnt) {
+    double s = 0.0;
+    for (int k = 0; k < cnt; ++k) s += __ldcg(part + p0 + k);
+    return s;
+}
+
+// Block-wide sum written as this item's partial.
+__device__ __forceinline__ void item_partial(double v, double* part, int64_t item, double* red) {
+    v = lk::block_sum(v, red);
+    if (threadIdx.x == 0) part[item] = v;
+}
+
+// ---- phases ----------------------------------------------------------------
+
+// INIT rows: alpha = 0, r = y, partial |y|^2.
+__device__ void ph_init(const BArgs& a, double* red) {
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const BInst& I = a.inst[a.row_inst[it]];
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        double yy = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
+            const double yi = I.y[i];
+            I.alpha[i] = 0.0;
+            I.r[i] = yi;
+            yy = fma(yi, yi, yy);
+        }
+        item_partial(yy, a.part, it, red);
+    }
+}
+
+// t = U^T r for CCCP instances: one direction per warp.
+template <typename PT>
+__device__ void ph_utr(const BArgs& a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < a.k_items; it += gridDim.x) {
+        const int ii = a.k_inst[it];
+        if (!running(a, ii)) continue;
+        const BInst& I = a.inst[ii];
+        const int k = (int)(it - I.kit0) * KB + warp;
+        if (k >= I.n_r) continue;
+        const PT* u = (const PT*)I.UT + (int64_t)k * I.ldu;
+        double s = 0.0;
+        for (int64_t i = lane; i < I.n; i += 32) s = fma((double)u[i], __ldcg(I.r + i), s);
+        s = lk::warp_sum(s);
+        if (lane == 0) I.t[k] = s;
+    }
+}
+
+// z = P r and partial r^T z.
+template <typename PT>
+__device__ void ph_precond(const BArgs& a, double* red, double* ts) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const int ii = a.row_inst[it];
+        if (!running(a, ii)) continue;
+        const BInst& I = a.inst[ii];
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        double rz = 0.0;
+        if (I.kind == PRECOND_CCCP) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < I.n_r; k += BT) ts[k] = __ldcg(I.t + k);
+            __syncthreads();
+            const PT* W = (const PT*)I.W;
+            for (int64_t i = i0 + warp; i < i1; i += BW) {
+                double s = 0.0;
+                for (int k = lane; k < I.n_r; k += 32) s = fma((double)W[i * I.n_r + k], ts[k], s);
+                s = lk::warp_sum(s);
+                if (lane == 0) {
+                    const double ri = __ldcg(I.r + i);
+                    const double zi = fma(I.cinv, ri, s);
+                    I.z[i] = zi;
+                    rz = fma(ri, zi, rz);
+                }
+            }
+        } else {
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
+                const double ri = __ldcg(I.r + i);
+                const double zi = (I.kind == PRECOND_JACOBI) ? ri * I.dinv[i] : ri;
+                I.z[i] = zi;
+                rz = fma(ri, zi, rz);
+            }
+        }
+        item_partial(rz, a.part, it, red);
+    }
+}
+
+// p = z + beta p (beta = 0 on the first pass), float32 copy for the product.
+__device__ void ph_newdir(const BArgs& a, bool first) {
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const int ii = a.row_inst[it];
+        if (!running(a, ii)) continue;
+        const BInst& I = a.inst[ii];
+        const double beta = first ? 0.0 : __ldcg(&a.sc[ii].beta);
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
+            const double pi = first ? __ldcg(I.z + i) : fma(beta, __ldcg(I.p + i), __ldcg(I.z + i));
+            I.p[i] = pi;
+            if (a.mixed) I.pf[i] = (float)pi;
+        }
+    }
+}
+
+// w = (lambda I + G) p over the materialised G, partial p^T w.
+__device__ void ph_matvec(const BArgs& a, double* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const int ii = a.row_inst[it];
+        if (!running(a, ii)) continue;
+        const BInst& I = a.inst[ii];
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        double pw = 0.0;
+        for (int64_t i = i0 + warp; i < i1; i += BW) {
+            double s;
+            if (a.mixed) {
+                const float4* k4 = reinterpret_cast<const float4*>(I.K32 + i * I.ldk);
+                const float4* p4 = reinterpret_cast<const float4*>(I.pf);
+                float acc0 = 0.f, acc1 = 0.f;
+                const int64_t n4 = I.ldk / 4;
+                int64_t j = lane;
+                for (; j + 32 < n4; j += 64) {
+                    const float4 ka = __ldg(k4 + j), pa = __ldcg(p4 + j);
+                    const float4 kb = __ldg(k4 + j + 32), pb = __ldcg(p4 + j + 32);
+                    acc0 = fmaf(ka.x, pa.x, fmaf(ka.y, pa.y, fmaf(ka.z, pa.z, fmaf(ka.w, pa.w, acc0))));
+                    acc1 = fmaf(kb.x, pb.x, fmaf(kb.y, pb.y, fmaf(kb.z, pb.z, fmaf(kb.w, pb.w, acc1))));
+                }
+                for (; j < n4; j += 32) {
+                    const float4 ka = __ldg(k4 + j), pa = __ldcg(p4 + j);
+                    acc0 = fmaf(ka.x, pa.x, fmaf(ka.y, pa.y, fmaf(ka.z, pa.z, fmaf(ka.w, pa.w, acc0))));
+                }
+                s = lk::warp_sum((double)acc0 + (double)acc1);
+            } else {
+                const double* k = I.K64 + i * I.ldk;
+                double acc = 0.0;
+                for (int64_t j = lane; j < I.n; j += 32) acc = fma(k[j], __ldcg(I.p + j), acc);
+                s = lk::warp_sum(acc);
+            }
+            if (lane == 0) {
+                const double pi = __ldcg(I.p + i);
+                const double wi = fma(I.lambda, pi, s);
+                I.w[i] = wi;
+                pw = fma(pi, wi, pw);
+            }
+        }
+        item_partial(pw, a.part, it, red);
+    }
+}
+
+// alpha += delta p, r -= delta w, partial |r|^2.
+__device__ void ph_update(const BArgs& a, double* red) {
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const int ii = a.row_inst[it];
+        if (!running(a, ii)) continue;
+        const BInst& I = a.inst[ii];
+        const double delta = __ldcg(&a.sc[ii].delta);
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        double rr = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
+            I.alpha[i] = fma(delta, __ldcg(I.p + i), __ldcg(I.alpha + i));
+            const double ri = fma(-delta, __ldcg(I.w + i), __ldcg(I.r + i));
+            I.r[i] = ri;
+            rr = fma(ri, ri, rr);
+        }
+        item_partial(rr, a.part, it, red);
+    }
+}
+
+// r = y - (lambda I + G) alpha with G = hi + lo in float64 arithmetic, for the
+// instances due for a true residual; partial |r|^2.
+__device__ void ph_true(const BArgs& a, double* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const int ii = a.row_inst[it];
+        if (!running(a, ii) || !*(volatile const int*)&a.sc[ii].need_true) continue;
+        const BInst& I = a.inst[ii];
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        double rr = 0.0;
+        for (int64_t i = i0 + warp; i < i1; i += BW) {
+            const float* h = I.K32 + i * I.ldk;
+            const float* l = I.K32lo + i * I.ldk;
+            double acc = 0.0;
+            for (int64_t j = lane; j < I.n; j += 32) acc = fma((double)h[j] + (double)l[j], __ldcg(I.alpha + j), acc);
+            acc = lk::warp_sum(acc);
+            if (lane == 0) {
+                const double ri = I.y[i] - fma(I.lambda, __ldcg(I.alpha + i), acc);
+                I.r[i] = ri;
+                rr = fma(ri, ri, rr);
+            }
+        }
+        item_partial(rr, a.part, it, red);
+    }
+}
+
+// |y - (lambda I + G) alpha|^2 at float64 accuracy for every instance (the
+// reported true residual): float64 G, or hi + lo for mixed instances.
+__device__ void ph_final(const BArgs& a, double* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
+        const BInst& I = a.inst[a.row_inst[it]];
+        const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
+        double rr = 0.0;
+        for (int64_t i = i0 + warp; i < i1; i += BW) {
+            double acc = 0.0;
+            if (a.mixed) {
+                const float* h = I.K32 + i * I.ldk;
+                const float* l = I.K32lo + i * I.ldk;
+                for (int64_t j = lane; j < I.n; j += 32) acc = fma((double)h[j] + (double)l[j], __ldcg(I.alpha + j), acc);
+            } else {
+                const double* k = I.K64 + i * I.ldk;
+                for (int64_t j = lane; j < I.n; j += 32) acc = fma(k[j], __ldcg(I.alpha + j), acc);
+            }
+            acc = lk::warp_sum(acc);
+            if (lane == 0) {
+                const double e = I.y[i] - fma(I.lambda, __ldcg(I.alpha + i), acc);
+                rr = fma(e, e, rr);
+            }
+        }
+        item_partial(rr, a.part, it, red);
+    }
+}
+
+// ---- per-instance scalar steps (one thread per instance) -------------------
+
+__device__ void sc_init(const BArgs& a, double tol) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+        const BInst& I = a.inst[i];
+        BScal& s = a.sc[i];
+        s.yy = sum_items(a.part, I.row0, I.rows);
+        s.tol2yy = tol * tol * s.yy;
+        s.iters = 0;
+        s.true_count = 0;
+        s.need_true = 0;
+        s.rr = s.yy;
+        s.rr_true = s.yy;
+        s.converged = 0;
+        if (!(s.yy > 0.0)) finish(s, isfinite(s.yy) ? 1 : 2);   // y = 0: alpha = 0 is exact
+    }
+}
+
+__device__ void sc_rz(const BArgs& a, bool first) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+        if (!running(a, i)) continue;
+        const BInst& I = a.inst[i];
+        BScal& s = a.sc[i];
+        const double tot = sum_items(a.part, I.row0, I.rows);
+        if (!isfinite(tot) || tot < 0.0) { finish(s, 2); continue; }
+        if (tot == 0.0) { finish(s, 1); continue; }
+        s.beta = (!first && s.rz > 0.0) ? tot / s.rz : 0.0;
+        s.rz = tot;
+    }
+}
+
+__device__ void sc_delta(const BArgs& a) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+        if (!running(a, i)) continue;
+        const BInst& I = a.inst[i];
+        BScal& s = a.sc[i];
+        const double pAp = sum_items(a.part, I.row0, I.rows);
+        s.pAp = pAp;
+        s.iters += 1;
+        if (!(pAp > 0.0) || !isfinite(pAp)) { s.delta = 0.0; finish(s, 2); continue; }
+        s.delta = s.rz / pAp;
+    }
+}
+
+__device__ void sc_stop(const BArgs& a, int* need_cnt) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+        if (!running(a, i)) continue;
+        const BInst& I = a.inst[i];
+        BScal& s = a.sc[i];
+        const double tot = sum_items(a.part, I.row0, I.rows);
+        s.rr = tot;
+        const bool small = tot <= s.tol2yy;
+        if (!isfinite(tot)) {
+            finish(s, 2);
+        } else if (!a.mixed || a.refine_every == 0) {
+            if (small) finish(s, 1);
+            else if (s.iters >= a.max_iter) finish(s, 3);
+        } else if (small || (s.iters % a.refine_every) == 0 || s.iters >= a.max_iter) {
+            s.need_true = 1;
+            atomicAdd(need_cnt, 1);
+        }
+    }
+}
+
+__device__ void sc_true(const BArgs& a) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+        if (!running(a, i)) continue;
+        BScal& s = a.sc[i];
+        if (!s.need_true) continue;
+        const BInst& I = a.inst[i];
+        const double tot = sum_items(a.part, I.row0, I.rows);
+        s.rr = tot;
+        s.rr_true = tot;
+        s.true_count += 1;
+        s.need_true = 0;
+        if (!isfinite(tot)) finish(s, 2);
+        else if (tot <= s.tol2yy) finish(s, 1);
+        else if (s.iters >= a.max_iter) finish(s, 3);
+    }
+}
+
+__device__ void sc_final(const BArgs& a) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+        const BInst& I = a.inst[i];
+        a.sc[i].rr_true = sum_items(a.part, I.row0, I.rows);
+    }
+}
+
+__device__ void count_active(const BArgs& a, int* active) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT)
+        if (running(a, i)) atomicAdd(active, 1);
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BT)
+k_batch_pcg(BArgs a, double tol) {
+    __shared__ double red[BW];
+    __shared__ double ts[LK_MAX_NR];
+    BGlobal* g = a.g;
+    int* err = &g->err;
+    auto sync = [&]() { return lk::grid_sync(&g->gs, err); };
+    if (blockIdx.x == 0 && threadIdx.x == 0) g->t0 = globaltimer();
+    ph_init(a, red);
+    if (!sync()) return;
+    sc_init(a, tol);
+    if (!sync()) return;
+    ph_utr<PT>(a);
+    if (!sync()) return;
+    ph_precond<PT>(a, red, ts);
+    if (!sync()) return;
+    sc_rz(a, true);
+    if (!sync()) return;
+    ph_newdir(a, true);
+    if (blockIdx.x == 0 && threadIdx.x == 0) { g->active[0] = 0; g->need_true[0] = 0; }
+    if (!sync()) return;
+    for (int iter = 0;; ++iter) {
+        const int par = iter & 1;
+        ph_matvec(a, red);
+        if (!sync()) return;
+        sc_delta(a);
+        if (blockIdx.x == 0 && threadIdx.x == 0) { g->active[par ^ 1] = 0; g->need_true[par ^ 1] = 0; }
+        if (!sync()) return;
+        ph_update(a, red);
+        if (!sync()) return;
+        sc_stop(a, &g->need_true[par]);
+        if (!sync()) return;
+        if (*(volatile int*)&g->need_true[par] > 0) {
+            ph_true(a, red);
+            if (!sync()) return;
+            sc_true(a);
+            if (!sync()) return;
+        }
+        ph_utr<PT>(a);
+        if (!sync()) return;
+        ph_precond<PT>(a, red, ts);
+        if (!sync()) return;
+        sc_rz(a, false);
+        count_active(a, &g->active[par]);
+        if (!sync()) return;
+        if (*(volatile int*)&g->active[par] == 0) break;
+        ph_newdir(a, false);
+        if (!sync()) return;
+    }
+    ph_final(a, red);
+    if (!sync()) return;
+    sc_final(a);
+}
+
+struct BatchTune {
+    int R = 32;
+    int per_sm = 2;
+    int64_t key = -1;
+};
+BatchTune g_tune;   // last autotuned choice (per process; keyed by the batch shape)
+
+}  // namespace
+
+// Launch the persistent batched solve once with rows-per-item R and per_sm CTAs
+// per SM; returns the device time in ms through *ms (may be NULL).
+static laker_status batch_launch(laker_ctx* ctx, const std::vector<BInst>& hin, bool fp64_prec, int R, int per_sm,
+                                 double tol, int max_iter, int refine_every, BScal* dsc, BGlobal* dg,
+                                 double* ms) {
+    const int count = (int)hin.size();
+    std::vector<BInst> inst = hin;
+    std::vector<int> row_inst, k_inst;
+    for (int i = 0; i < count; ++i) {
+        BInst& I = inst[i];
+        I.rows = (int)((I.n + R - 1) / R);
+        I.row0 = (int64_t)row_inst.size();
+        row_inst.insert(row_inst.end(), I.rows, i);
+        I.kits = (I.kind == PRECOND_CCCP) ? (I.n_r + KB - 1) / KB : 0;
+        I.kit0 = (int64_t)k_inst.size();
+        k_inst.insert(k_inst.end(), I.kits, i);
+    }
+    if (k_inst.empty()) k_inst.push_back(0);   // keeps the array non-empty; k_items counts the real items
+    BInst* dinst = nullptr;
+    int *drow = nullptr, *dk = nullptr;
+    double* part = nullptr;
+    laker_status st;
+    auto cleanup = [&]() { cudaFree(dinst); cudaFree(drow); cudaFree(dk); cudaFree(part); };
+    if ((st = lk_malloc(ctx, (void**)&dinst, sizeof(BInst) * count)) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&drow, sizeof(int) * row_inst.size())) != LAKER_OK) { cleanup(); return st; }
+    if ((st = lk_malloc(ctx, (void**)&dk, sizeof(int) * k_inst.size())) != LAKER_OK) { cleanup(); return st; }
+    if ((st = lk_malloc(ctx, (void**)&part, sizeof(double) * row_inst.size())) != LAKER_OK) { cleanup(); return st; }
+    cudaStream_t s = ctx->stream;
+    LK_CUDA(ctx, cudaMemcpyAsync(dinst, inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
+    LK_CUDA(ctx, cudaMemcpyAsync(drow, row_inst.data(), sizeof(int) * row_inst.size(), cudaMemcpyHostToDevice, s));
+    LK_CUDA(ctx, cudaMemcpyAsync(dk, k_inst.data(), sizeof(int) * k_inst.size(), cudaMemcpyHostToDevice, s));
+    LK_CUDA(ctx, cudaMemsetAsync(dg, 0, sizeof(BGlobal), s));
+    BArgs a{};
+    a.count = count;
+    a.inst = dinst;
+    a.sc = dsc;
+    a.row_inst = drow;
+    a.row_items = (int64_t)row_inst.size();
+    a.k_inst = dk;
+    int64_t kits = 0;
+    for (const BInst& I : inst) kits += I.kits;
+    a.k_items = kits;
+    a.R = R;
+    a.part = part;
+    a.g = dg;
+    a.max_iter = max_iter;
+    a.refine_every = refine_every;
+    a.mixed = fp64_prec ? 0 : 1;
+    const void* fn = fp64_prec ? (const void*)k_batch_pcg<double> : (const void*)k_batch_pcg<float>;
+    int occ = 0;
+    LK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT, 0));
+    if (occ < 1) { cleanup(); return set_error(ctx, LAKER_ERR_CUDA, "batched kernel cannot be resident"); }
+    const int grid = std::min(per_sm, occ) * ctx->num_sms;
+    void* args[] = {&a, &tol};
+    cudaEvent_t e0, e1;
+    LK_CUDA(ctx, cudaEventCreate(&e0));
+    LK_CUDA(ctx, cudaEventCreate(&e1));
+    LK_CUDA(ctx, cudaEventRecord(e0, s));
+    LK_CUDA(ctx, cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BT), args, 0, s));
+    LK_LAUNCHED(ctx);
+    LK_CUDA(ctx, cudaEventRecord(e1, s));
+    LK_CUDA(ctx, cudaEventSynchronize(e1));
+    float t = 0.f;
+    LK_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms) *ms = t;
+    cleanup();
+    int herr = 0;
+    LK_CUDA(ctx, cudaMemcpy(&herr, &dg->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return set_error(ctx, (laker_status)herr, "batched PCG: grid barrier timed out");
+    return LAKER_OK;
+}
+
+laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items, double tol, int max_iter,
+                               int refine_every, laker_solve_info* infos, double* done_ms) {
+    bool fp64_prec = items[0].op->precision == LAKER_FP64;
+    for (int i = 0; i < count; ++i) {
+        const laker_op* op = items[i].op;
+        if ((op->precision == LAKER_FP64) != fp64_prec)
+            return set_error(ctx, LAKER_ERR_ARG, "batched solve: all operators need the same precision class");
+        if (fp64_prec ? op->K64 == nullptr : (op->K32 == nullptr || op->K32lo == nullptr))
+            return set_error(ctx, LAKER_ERR_UNSUPPORTED, "batched solve: needs materialised operators");
+        const laker_precond* P = items[i].P;
+        if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "batched solve: preconditioner size mismatch");
+        if (P && P->kind == PRECOND_CCCP && (fp64_prec ? P->UT64 == nullptr : P->UT32 == nullptr))
+            return set_error(ctx, LAKER_ERR_UNSUPPORTED, "batched solve: preconditioner precision differs");
+    }
+    // workspace: r, z, p, w per instance, float32 p copies, U^T r vectors
+    int64_t nsum = 0, ldsum = 0, nrsum = 0;
+    for (int i = 0; i < count; ++i) {
+        nsum += items[i].op->n;
+        ldsum += items[i].op->ldk;
+        nrsum += (items[i].P && items[i].P->kind == PRECOND_CCCP) ? items[i].P->n_r : 0;
+    }
+    double* vec = nullptr;
+    float* pf = nullptr;
+    double* tv = nullptr;
+    BScal* dsc = nullptr;
+    BGlobal* dg = nullptr;
+    laker_status st;
+    auto cleanup = [&]() { cudaFree(vec); cudaFree(pf); cudaFree(tv); cudaFree(dsc); cudaFree(dg); };
+    if ((st = lk_malloc(ctx, (void**)&vec, sizeof(double) * 4 * nsum)) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&pf, sizeof(float) * ldsum)) != LAKER_OK) { cleanup(); return st; }
+    if ((st = lk_malloc(ctx, (void**)&tv, sizeof(double) * std::max<int64_t>(1, nrsum))) != LAKER_OK) {
+        cleanup();
+        return st;
+    }
+    if ((st = lk_malloc(ctx, (void**)&dsc, sizeof(BScal) * count)) != LAKER_OK) { cleanup(); return st; }
+    if ((st = lk_malloc(ctx, (void**)&dg, sizeof(BGlobal))) != LAKER_OK) { cleanup(); return st; }
+    LK_CUDA(ctx, cudaMemsetAsync(pf, 0, sizeof(float) * ldsum, ctx->stream));
+    std::vector<BInst> hin(count);
+    int64_t off = 0, offp = 0, offt = 0;
+    for (int i = 0; i < count; ++i) {
+        const laker_op* op = items[i].op;
+        const laker_precond* P = items[i].P;
+        BInst& I = hin[i];
+        I = BInst{};
+        I.n = op->n;
+        I.ldk = op->ldk;
+        I.lambda = op->lambda;
+        I.K32 = op->K32;
+        I.K32lo = op->K32lo;
+        I.K64 = op->K64;
+        I.kind = P ? P->kind : PRECOND_IDENTITY;
+        if (I.kind == PRECOND_CCCP) {
+            I.n_r = P->n_r;
+            I.ldu = P->ldu;
+            I.cinv = P->cinvsqrt;
+            I.UT = fp64_prec ? (const void*)P->UT64 : (const void*)P->UT32;
+            I.W = fp64_prec ? (const void*)P->W64 : (const void*)P->W32;
+            I.t = tv + offt;
+            offt += P->n_r;
+        }
+        if (I.kind == PRECOND_JACOBI) I.dinv = P->dinv;
+        I.y = items[i].y;
+        I.alpha = items[i].alpha;
+        I.r = vec + off;
+        I.z = vec + off + nsum;
+        I.p = vec + off + 2 * nsum;
+        I.w = vec + off + 3 * nsum;
+        I.pf = pf + offp;
+        off += op->n;
+        offp += op->ldk;
+    }
+    // autotune rows per item and CTAs per SM once per batch shape: 8 products
+    // per candidate, then keep the fastest (the real solve re-initialises)
+    const int64_t key = nsum * 4099 + count;
+    if (g_tune.key != key) {
+        double best = 1e300;
+        BatchTune pick;
+        for (int R : {16, 32, 64})
+            for (int per_sm : {1, 2}) {
+                double ms = 0.0;
+                if ((st = batch_launch(ctx, hin, fp64_prec, R, per_sm, tol, 8, refine_every, dsc, dg, &ms)) !=
+                    LAKER_OK) {
+                    cleanup();
+                    return st;
+                }
+                if (ms < best) { best = ms; pick.R = R; pick.per_sm = per_sm; }
+            }
+        pick.key = key;
+        g_tune = pick;
+    }
+    if ((st = batch_launch(ctx, hin, fp64_prec, g_tune.R, g_tune.per_sm, tol, max_iter, refine_every, dsc, dg,
+                           nullptr)) != LAKER_OK) {
+        cleanup();
+        return st;
+    }
+    std::vector<BScal> hs(count);
+    BGlobal hg{};
+    LK_CUDA(ctx, cudaMemcpy(hs.data(), dsc, sizeof(BScal) * count, cudaMemcpyDeviceToHost));
+    LK_CUDA(ctx, cudaMemcpy(&hg, dg, sizeof(BGlobal), cudaMemcpyDeviceToHost));
+    laker_status worst = LAKER_OK;
+    for (int i = 0; i < count; ++i) {
+        const BScal& s = hs[i];
+        laker_status si = LAKER_OK;
+        if (s.converged == 2) si = LAKER_ERR_BREAKDOWN;
+        else if (s.converged == 3 || s.converged == 0) si = LAKER_ERR_MAXITER;
+        if (infos) {
+            laker_solve_info& f = infos[i];
+            f.iterations = s.iters;
+            f.true_residuals = s.true_count;
+            f.converged = s.converged == 1;
+            f.rel_res = s.yy > 0.0 ? std::sqrt(s.rr / s.yy) : 0.0;
+            f.rel_res_true = s.yy > 0.0 ? std::sqrt(s.rr_true / s.yy) : 0.0;
+            f.status = si;
+        }
+        if (done_ms) done_ms[i] = (s.t_done > hg.t0) ? (double)(s.t_done - hg.t0) * 1e-6 : 0.0;
+        if (si == LAKER_ERR_BREAKDOWN) worst = si;
+        else if (si == LAKER_ERR_MAXITER && worst == LAKER_OK) worst = si;
+    }
+    cleanup();
+    if (worst != LAKER_OK) return set_error(ctx, worst, "batched PCG: some instances did not converge");
+    return LAKER_OK;
+}

@@ -65,4 +65,42 @@ __device__ __forceinline__ double sum_partials(const double* partials, int count
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident).  The wait is
+// bounded: after ~2 s it raises LAKER_ERR_TIMEOUT in *err, and once *err is
+// set every CTA leaves at its next barrier.  Returns false in that case.
+struct GridSync {
+    unsigned int count;
+    unsigned int gen;
+};
+constexpr long long GRID_SPIN_CYCLES = 4000000000ll;
+__device__ __forceinline__ bool grid_sync(GridSync* gs, int* err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* genp = &gs->gen;
+        const unsigned int g = *genp;
+        __threadfence();
+        if (atomicAdd(&gs->count, 1u) == gridDim.x - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            for (unsigned int spins = 1; *genp == g; ++spins) {
+                if ((spins & 63u) == 0) {
+                    if (*(volatile int*)err) break;
+                    if (clock64() - t0 > GRID_SPIN_CYCLES) {
+                        atomicExch(err, LAKER_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        ok_s = (*(volatile int*)err == 0);
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
 }  // namespace lk

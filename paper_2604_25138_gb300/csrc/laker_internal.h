@@ -126,6 +126,9 @@ void mf_release(laker_op* op);
 laker_status mf_status(laker_ctx* ctx, const laker_op* op);
 laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+// laker_batch.cu
+laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items, double tol, int max_iter,
+                               int refine_every, laker_solve_info* infos, double* done_ms);
 laker_status mf_matvec_launch(laker_ctx* ctx, const laker_op* op, const double* pin,
                               const double* z, double* pout, double* w, PcgScalars* sc,
                               double* partials, int fuse_p, float* pbuf, float* wbuf);

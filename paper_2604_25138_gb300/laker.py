@@ -41,6 +41,10 @@ class SolveInfo(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("P", ctypes.c_void_p), ("y", ctypes.c_void_p), ("alpha", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -62,6 +66,8 @@ def library() -> ctypes.CDLL:
         "laker_launch_count": (i64, [vp]),
         "laker_build_kernel": (i32, [vp, vp, i64, i32, f64, f64, i32, i32, pvp]),
         "laker_op_destroy": (i32, [vp]),
+        "laker_pcg_solve_batched": (i32, [vp, i32, ctypes.POINTER(BatchItem), f64, i32, i32,
+                                          ctypes.POINTER(SolveInfo), ctypes.POINTER(f64)]),
         "laker_op_matvec": (i32, [vp, vp, vp, vp]),
         "laker_op_matvec_fp64": (i32, [vp, vp, vp, vp]),
         "laker_op_time_operator": (i32, [vp, vp, vp, i32, ctypes.POINTER(f64)]),
@@ -259,6 +265,28 @@ def laker_pcg_solve(ctx: Context, op: Operator, P: Preconditioner | None, y: tor
                                        ctypes.byref(info))
     ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
     return alpha, {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+
+def laker_pcg_solve_batched(ctx: Context, items, tol: float, max_iter: int = 100000, refine_every: int = 0,
+                            allow_maxiter: bool = False):
+    """items: sequence of (op, P or None, y, alpha or None).  Returns the list of
+    alphas, the list of info dicts and the per-instance stop times in ms."""
+    count = len(items)
+    arr = (BatchItem * count)()
+    alphas = []
+    for k, (op, P, y, alpha) in enumerate(items):
+        if alpha is None:
+            alpha = torch.empty_like(y)
+        alphas.append(alpha)
+        arr[k] = BatchItem(op.handle, P.handle if P is not None else None, _ptr(y, "y", op.n),
+                           _ptr(alpha, "alpha", op.n))
+    infos = (SolveInfo * count)()
+    done = (ctypes.c_double * count)()
+    with ctx:
+        st = library().laker_pcg_solve_batched(ctx.handle, count, arr, tol, max_iter, refine_every, infos, done)
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    return (alphas, [{f: getattr(infos[k], f) for f, _ in SolveInfo._fields_} for k in range(count)],
+            [done[k] for k in range(count)])
 
 
 def laker_eval_map(ctx: Context, op: Operator, Qg: torch.Tensor, alpha: torch.Tensor,
