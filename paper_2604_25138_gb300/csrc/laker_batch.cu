@@ -14,7 +14,7 @@
 // a fixed order (deterministic).  Mixed instances (float32 G) replace r by
 // y - (lambda I + G) alpha computed in float64 from the float32 pair every
 // `refine_every` products and whenever the recursive residual passes, as the
-// single-instance solver does.
+// single-instance solver does (here with float64 products and sums).
 #include <algorithm>
 #include <chrono>
 #include <vector>
@@ -129,7 +129,17 @@ __device__ void ph_init(const BArgs& a, double* red) {
     }
 }
 
-// t = U^T r for CCCP instances: one direction per warp.
+// t = U^T r for CCCP instances: one direction per warp, four elements of its
+// row of U^T per lane and step (pitch ldu, a multiple of 4: 16-byte row
+// starts), two steps in flight.
+__device__ __forceinline__ void load4(const float* u, int64_t e, float* v) {
+    const float4 t = *reinterpret_cast<const float4*>(u + e);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* u, int64_t e, double* v) {
+    const double2 t0 = *reinterpret_cast<const double2*>(u + e), t1 = *reinterpret_cast<const double2*>(u + e + 2);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
 template <typename PT>
 __device__ void ph_utr(const BArgs& a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,9 +150,27 @@ __device__ void ph_utr(const BArgs& a) {
         const int k = (int)(it - I.kit0) * KB + warp;
         if (k >= I.n_r) continue;
         const PT* u = (const PT*)I.UT + (int64_t)k * I.ldu;
-        double s = 0.0;
-        for (int64_t i = lane; i < I.n; i += 32) s = fma((double)u[i], __ldcg(I.r + i), s);
-        s = lk::warp_sum(s);
+        double s0 = 0.0, s1 = 0.0;
+        const int64_t n4 = I.n / 4;
+        int64_t v = lane;
+        for (; v + 32 < n4; v += 64) {
+            PT ua[4], ub[4];
+            load4(u, 4 * v, ua);
+            load4(u, 4 * (v + 32), ub);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                s0 = fma((double)ua[c], __ldcg(I.r + 4 * v + c), s0);
+                s1 = fma((double)ub[c], __ldcg(I.r + 4 * (v + 32) + c), s1);
+            }
+        }
+        for (; v < n4; v += 32) {
+            PT ua[4];
+            load4(u, 4 * v, ua);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s0 = fma((double)ua[c], __ldcg(I.r + 4 * v + c), s0);
+        }
+        for (int64_t e = 4 * n4 + lane; e < I.n; e += 32) s1 = fma((double)u[e], __ldcg(I.r + e), s1);
+        const double s = lk::warp_sum(s0 + s1);
         if (lane == 0) I.t[k] = s;
     }
 }
@@ -162,15 +190,38 @@ __device__ void ph_precond(const BArgs& a, double* red, double* ts) {
             for (int k = threadIdx.x; k < I.n_r; k += BT) ts[k] = __ldcg(I.t + k);
             __syncthreads();
             const PT* W = (const PT*)I.W;
-            for (int64_t i = i0 + warp; i < i1; i += BW) {
-                double s = 0.0;
-                for (int k = lane; k < I.n_r; k += 32) s = fma((double)W[i * I.n_r + k], ts[k], s);
-                s = lk::warp_sum(s);
+            for (int64_t i = i0 + 4 * warp; i < i1; i += 4 * BW) {
+                const int nrow = (int)min((int64_t)4, i1 - i);
+                double s[4] = {0.0, 0.0, 0.0, 0.0};
+                int k = lane;
+                for (; k + 96 < I.n_r; k += 128) {
+                    PT wv[4][4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) wv[q][c] = (q < nrow) ? W[(i + q) * I.n_r + k + 32 * c] : PT(0);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const double tk = ts[k + 32 * c];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) s[q] = fma((double)wv[q][c], tk, s[q]);
+                    }
+                }
+                for (; k < I.n_r; k += 32) {
+                    const double tk = ts[k];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nrow) s[q] = fma((double)W[(i + q) * I.n_r + k], tk, s[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[q] = lk::warp_sum(s[q]);
                 if (lane == 0) {
-                    const double ri = __ldcg(I.r + i);
-                    const double zi = fma(I.cinv, ri, s);
-                    I.z[i] = zi;
-                    rz = fma(ri, zi, rz);
+                    for (int q = 0; q < nrow; ++q) {
+                        const double ri = __ldcg(I.r + i + q);
+                        const double zi = fma(I.cinv, ri, s[q]);
+                        I.z[i + q] = zi;
+                        rz = fma(ri, zi, rz);
+                    }
                 }
             }
         } else {
@@ -201,7 +252,12 @@ __device__ void ph_newdir(const BArgs& a, bool first) {
     }
 }
 
-// w = (lambda I + G) p over the materialised G, partial p^T w.
+// w = (lambda I + G) p over the materialised G, partial p^T w.  A warp takes
+// four rows at once: each 16-byte load of p serves four rows, and eight
+// 16-byte loads of G per lane are in flight.
+__device__ __forceinline__ float dot4(const float4 k, const float4 p, float acc) {
+    return fmaf(k.x, p.x, fmaf(k.y, p.y, fmaf(k.z, p.z, fmaf(k.w, p.w, acc))));
+}
 __device__ void ph_matvec(const BArgs& a, double* red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
@@ -210,36 +266,51 @@ __device__ void ph_matvec(const BArgs& a, double* red) {
         const BInst& I = a.inst[ii];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double pw = 0.0;
-        for (int64_t i = i0 + warp; i < i1; i += BW) {
-            double s;
+        for (int64_t i = i0 + 4 * warp; i < i1; i += 4 * BW) {
+            const int nrow = (int)min((int64_t)4, i1 - i);
+            double s[4];
             if (a.mixed) {
-                const float4* k4 = reinterpret_cast<const float4*>(I.K32 + i * I.ldk);
                 const float4* p4 = reinterpret_cast<const float4*>(I.pf);
-                float acc0 = 0.f, acc1 = 0.f;
+                const float4* k4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    k4[q] = reinterpret_cast<const float4*>(I.K32 + (i + (q < nrow ? q : 0)) * I.ldk);
+                float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f};
                 const int64_t n4 = I.ldk / 4;
                 int64_t j = lane;
                 for (; j + 32 < n4; j += 64) {
-                    const float4 ka = __ldg(k4 + j), pa = __ldcg(p4 + j);
-                    const float4 kb = __ldg(k4 + j + 32), pb = __ldcg(p4 + j + 32);
-                    acc0 = fmaf(ka.x, pa.x, fmaf(ka.y, pa.y, fmaf(ka.z, pa.z, fmaf(ka.w, pa.w, acc0))));
-                    acc1 = fmaf(kb.x, pb.x, fmaf(kb.y, pb.y, fmaf(kb.z, pb.z, fmaf(kb.w, pb.w, acc1))));
+                    const float4 pa = __ldcg(p4 + j), pb = __ldcg(p4 + j + 32);
+                    float4 ka[4], kb[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { ka[q] = __ldg(k4[q] + j); kb[q] = __ldg(k4[q] + j + 32); }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { acc[q] = dot4(ka[q], pa, acc[q]); acc2[q] = dot4(kb[q], pb, acc2[q]); }
                 }
                 for (; j < n4; j += 32) {
-                    const float4 ka = __ldg(k4 + j), pa = __ldcg(p4 + j);
-                    acc0 = fmaf(ka.x, pa.x, fmaf(ka.y, pa.y, fmaf(ka.z, pa.z, fmaf(ka.w, pa.w, acc0))));
+                    const float4 pa = __ldcg(p4 + j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = dot4(__ldg(k4[q] + j), pa, acc[q]);
                 }
-                s = lk::warp_sum((double)acc0 + (double)acc1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[q] = lk::warp_sum((double)acc[q] + (double)acc2[q]);
             } else {
-                const double* k = I.K64 + i * I.ldk;
-                double acc = 0.0;
-                for (int64_t j = lane; j < I.n; j += 32) acc = fma(k[j], __ldcg(I.p + j), acc);
-                s = lk::warp_sum(acc);
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int64_t j = lane; j < I.n; j += 32) {
+                    const double pj = __ldcg(I.p + j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nrow) acc[q] = fma(I.K64[(i + q) * I.ldk + j], pj, acc[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[q] = lk::warp_sum(acc[q]);
             }
             if (lane == 0) {
-                const double pi = __ldcg(I.p + i);
-                const double wi = fma(I.lambda, pi, s);
-                I.w[i] = wi;
-                pw = fma(pi, wi, pw);
+                for (int q = 0; q < nrow; ++q) {
+                    const double pi = __ldcg(I.p + i + q);
+                    const double wi = fma(I.lambda, pi, s[q]);
+                    I.w[i + q] = wi;
+                    pw = fma(pi, wi, pw);
+                }
             }
         }
         item_partial(pw, a.part, it, red);
@@ -266,7 +337,11 @@ __device__ void ph_update(const BArgs& a, double* red) {
 }
 
 // r = y - (lambda I + G) alpha with G = hi + lo in float64 arithmetic, for the
-// instances due for a true residual; partial |r|^2.
+// instances due for a true residual; partial |r|^2.  Near convergence the
+// terms G_ij alpha_j exceed the result by |alpha| / |y| ~ 1 / lambda (1e5 at
+// lambda = 1e-5): float64 products and sums keep the residual's noise two
+// orders below the 1e-6 test, where a split-float32 sum (2^-48 per term) does
+// not.  Two rows per warp share the loads of alpha.
 __device__ void ph_true(const BArgs& a, double* red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
@@ -275,16 +350,34 @@ __device__ void ph_true(const BArgs& a, double* red) {
         const BInst& I = a.inst[ii];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double rr = 0.0;
-        for (int64_t i = i0 + warp; i < i1; i += BW) {
-            const float* h = I.K32 + i * I.ldk;
-            const float* l = I.K32lo + i * I.ldk;
-            double acc = 0.0;
-            for (int64_t j = lane; j < I.n; j += 32) acc = fma((double)h[j] + (double)l[j], __ldcg(I.alpha + j), acc);
-            acc = lk::warp_sum(acc);
+        for (int64_t i = i0 + 2 * warp; i < i1; i += 2 * BW) {
+            const int nrow = (int)min((int64_t)2, i1 - i);
+            const float4* h0 = reinterpret_cast<const float4*>(I.K32 + i * I.ldk);
+            const float4* l0 = reinterpret_cast<const float4*>(I.K32lo + i * I.ldk);
+            const float4* h1 = reinterpret_cast<const float4*>(I.K32 + (i + nrow - 1) * I.ldk);
+            const float4* l1 = reinterpret_cast<const float4*>(I.K32lo + (i + nrow - 1) * I.ldk);
+            double s0 = 0.0, s1 = 0.0;
+            const int64_t n4 = I.ldk / 4;
+            for (int64_t v = lane; v < n4; v += 32) {
+                const float4 a0 = __ldcs(h0 + v), b0 = __ldcs(l0 + v), a1 = __ldcs(h1 + v), b1 = __ldcs(l1 + v);
+                const float ha[4] = {a0.x, a0.y, a0.z, a0.w}, la[4] = {b0.x, b0.y, b0.z, b0.w};
+                const float hb[4] = {a1.x, a1.y, a1.z, a1.w}, lb[4] = {b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int64_t j = 4 * v + c;
+                    const double x = j < I.n ? __ldcg(I.alpha + j) : 0.0;
+                    s0 = fma((double)ha[c] + (double)la[c], x, s0);
+                    s1 = fma((double)hb[c] + (double)lb[c], x, s1);
+                }
+            }
+            s0 = lk::warp_sum(s0);
+            s1 = lk::warp_sum(s1);
             if (lane == 0) {
-                const double ri = I.y[i] - fma(I.lambda, __ldcg(I.alpha + i), acc);
-                I.r[i] = ri;
-                rr = fma(ri, ri, rr);
+                for (int q = 0; q < nrow; ++q) {
+                    const double ri = I.y[i + q] - fma(I.lambda, __ldcg(I.alpha + i + q), q == 0 ? s0 : s1);
+                    I.r[i + q] = ri;
+                    rr = fma(ri, ri, rr);
+                }
             }
         }
         item_partial(rr, a.part, it, red);

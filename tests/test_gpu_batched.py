@@ -114,6 +114,7 @@ def test_batched_mixed_reaches_true_tolerance(L, ctx):
         lam = float(10 ** rng.uniform(-5, -2))
         spec.append((n, d, lam))
     spec.append((40, 16, 1e-3))                 # a tiny ragged one
+    spec.append((6000, 32, 1e-5))               # |alpha| ~ 1e5: the residual needs all of alpha's bits
     insts = _batch_instances(spec, 800)
     items, keep, refs = [], [], []
     for inst in insts:
