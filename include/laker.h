@@ -60,6 +60,7 @@ typedef enum {
 typedef struct laker_ctx laker_ctx;
 typedef struct laker_op laker_op;
 typedef struct laker_precond laker_precond;
+typedef struct laker_setnet laker_setnet;
 
 typedef struct {
     int iterations;      /* CCCP updates applied */
@@ -206,6 +207,66 @@ typedef struct {
 laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items,
                                      double tol, int max_iter, int refine_every,
                                      laker_solve_info* infos, double* done_ms);
+
+/*
+ * Learned set-to-parameters network (no counterpart in the paper, whose only
+ * learning is the CCCP fit of Sec. IV-B..D).  It reads an instance as a set of
+ * points x_i = [location / L (2), q_i (d), y_i] and predicts log c and the
+ * per-direction log D_k of Sigma_* = c I + U diag(D) U^T:
+ *   h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), h3 = tanh(h2 W3 + b3);
+ *   z = mean over the points of h3;
+ *   log c = tanh(z Wg1 + bg1) . wg2 + bg2;
+ *   log D_k = tanh([z, f_k] Wd1 + bd1) . wd2 + bd2 with the direction
+ *   features f_k = [log |u_k|, sum_j M_kj^2] (laker_precond_direction_features).
+ * Loss over a batch of B instances:
+ *   (1/B) sum_b [(log c_b - t_b)^2 + (1/K_b) sum_k (log D_bk - T_bk)^2].
+ * Weights: float32 masters, used in bf16; float32 activations and sums; Adam
+ * (beta 0.9 / 0.999, eps 1e-8).  Parameters form one float32 vector laid out
+ * as W1, b1, W2, b2, W3, b3, Wg1, bg1, wg2, bg2, Wd1, bd1, wd2, bd2 (matrices
+ * row-major, input dimension first); Glorot-uniform from `seed`, zero biases.
+ * A batch passes its points as one device array X (P x in_dim float32;
+ * instance b owns rows poff[b] .. poff[b+1]-1) and its directions as F
+ * (K x 2 float32, rows koff[b] .. koff[b+1]-1); poff and koff are HOST
+ * arrays of B + 1 ints starting at 0; every instance needs at least one point.
+ */
+laker_status laker_setnet_create(laker_ctx* ctx, int in_dim, int hidden, int dir_hidden, uint64_t seed,
+                                 laker_setnet** net);
+laker_status laker_setnet_destroy(laker_setnet* net);
+int64_t laker_setnet_num_params(const laker_setnet* net);
+/* host float32 arrays of laker_setnet_num_params entries; set resets Adam */
+laker_status laker_setnet_get_params(laker_ctx* ctx, const laker_setnet* net, float* host);
+laker_status laker_setnet_set_params(laker_ctx* ctx, laker_setnet* net, const float* host);
+/* X (device, n x (d + 3) float32) = [loc (n x 2), Q (n x d), y (n)] (device float64 inputs) */
+laker_status laker_setnet_point_features(laker_ctx* ctx, int64_t n, int d, const double* loc, const double* Q,
+                                         const double* y, float* X);
+/* logc (device, B) and logD (device, koff[B]); either may be NULL */
+laker_status laker_setnet_forward(laker_ctx* ctx, laker_setnet* net, int B, const float* X, const int* poff,
+                                  const float* F, const int* koff, float* logc, float* logD);
+/* gradient of the loss (device, num_params) at targets tc (device, B), tD
+ * (device, koff[B]); *loss (host) receives the loss; no update */
+laker_status laker_setnet_gradient(laker_ctx* ctx, laker_setnet* net, int B, const float* X, const int* poff,
+                                   const float* F, const int* koff, const float* tc, const float* tD, float* grad,
+                                   float* loss);
+/* one Adam step with learning rate lr on the batch; *loss (host) before the step */
+laker_status laker_setnet_train_step(laker_ctx* ctx, laker_setnet* net, int B, const float* X, const int* poff,
+                                     const float* F, const int* koff, const float* tc, const float* tD, float lr,
+                                     float* loss);
+/* F (device, n_r x 2 float32) = [log |u_k|, sum_j M_kj^2] of a CCCP preconditioner's directions */
+laker_status laker_precond_direction_features(laker_ctx* ctx, const laker_precond* P, float* F);
+/*
+ * CCCP fit started from, or replaced by, the network's prediction (Sec. IV-D
+ * iteration; the prediction is an extension beyond the paper).  After the
+ * directions U and their Gram M are formed, the network predicts (c, D) from
+ * the point features X (device, n x in_dim, laker_setnet_point_features) and
+ * the direction features; the prediction is scaled to tr Sigma = n.
+ *   mode 0: CCCP iterations start from the prediction (warm start);
+ *   mode 1: the prediction is used as Sigma_* (no CCCP iteration).
+ * Other arguments as laker_fit_preconditioner.
+ */
+laker_status laker_fit_preconditioner_learned(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
+                                              double gamma, double rho, double eps, int max_iter, double tol,
+                                              laker_setnet* net, const float* X, int mode, laker_precond** P,
+                                              laker_fit_info* info);
 
 /*
  * Radio-map reconstruction (Sec. III-A, Eq. sc-radio-map-reconstruction;

@@ -57,6 +57,7 @@ void free_precond(laker_precond* P) {
     cudaFree(P->UT64);
     cudaFree(P->W32);
     cudaFree(P->dinv);
+    cudaFree(P->feat);
     delete P;
 }
 
@@ -222,6 +223,40 @@ laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const 
     st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info);
     if (st != LAKER_OK) { free_precond(P); return st; }
     *out = P;
+    return LAKER_OK;
+}
+
+laker_status laker_fit_preconditioner_learned(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
+                                              double gamma, double rho, double eps, int max_iter, double tol,
+                                              laker_setnet* net, const float* X, int mode, laker_precond** out,
+                                              laker_fit_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !Z || !out || !net || !X) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (mode != 0 && mode != 1) return set_error(ctx, LAKER_ERR_ARG, "mode must be 0 (warm start) or 1 (direct)");
+    if (setnet_in_dim(net) != op->d + 3) return set_error(ctx, LAKER_ERR_ARG, "set network input size is not d + 3");
+    if (n_r < 1 || n_r > LK_MAX_NR) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 2048");
+    if (!(gamma >= 0.0) || !(eps > 0.0) || rho > 1.0 || max_iter < 1 || !(tol >= 0.0))
+        return set_error(ctx, LAKER_ERR_ARG, "bad CCCP parameters");
+    if ((st = scan_finite(ctx, Z, op->n * (int64_t)n_r)) != LAKER_OK) return st;
+    laker_precond* P = new (std::nothrow) laker_precond();
+    if (!P) return LAKER_ERR_OOM;
+    P->ctx = ctx;
+    P->use32 = op->precision != LAKER_FP64;
+    st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info, net, X, mode);
+    if (st != LAKER_OK) { free_precond(P); return st; }
+    *out = P;
+    return LAKER_OK;
+}
+
+laker_status laker_precond_direction_features(laker_ctx* ctx, const laker_precond* P, float* F) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!P || !F) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (P->kind != PRECOND_CCCP || !P->feat) return set_error(ctx, LAKER_ERR_ARG, "not a CCCP preconditioner");
+    LK_CUDA(ctx, cudaMemcpyAsync(F, P->feat, sizeof(float) * 2 * P->n_r, cudaMemcpyDeviceToDevice, ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return LAKER_OK;
 }
 

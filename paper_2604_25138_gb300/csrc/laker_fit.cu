@@ -164,6 +164,18 @@ __global__ void k_colscale(int64_t n, int n_r, double* __restrict__ U, const dou
     U[idx] *= inv[idx % n_r];
 }
 
+// Direction features of the learned start: F[k] = [log |u_k|, sum_j M_kj^2]
+// (inv[k] = 1/|u_k| from k_colnorm; M the Gram of the unit directions).
+__global__ void k_dir_features(int nr, const double* __restrict__ inv, const double* __restrict__ M,
+                               float* __restrict__ F) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    double s = 0.0;
+    for (int j = 0; j < nr; ++j) s = fma(M[(int64_t)k * nr + j], M[(int64_t)k * nr + j], s);
+    F[2 * k] = (float)(inv[k] > 0.0 ? -log(inv[k]) : 0.0);
+    F[2 * k + 1] = (float)s;
+}
+
 // ---------------------------------------------------------------------------
 // CCCP state and kernels (padded size NP = round_up(N_r, 32))
 // ---------------------------------------------------------------------------
@@ -527,7 +539,8 @@ unsigned gsz(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b
 }  // namespace
 
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma, double rho,
-                      double eps, int max_iter, double tol, laker_precond* P, laker_fit_info* info) {
+                      double eps, int max_iter, double tol, laker_precond* P, laker_fit_info* info, laker_setnet* net,
+                      const float* Xpts, int mode) {
     const int64_t n = op->n;
     const int nr = n_r;
     const int NP = (nr + NB - 1) / NB * NB;
@@ -570,12 +583,38 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         return st;
     // ---- shrinkage-regularised CCCP
     if (rho < 0.0) rho = (nr >= n) ? 1e-3 : std::min(0.5, std::max(1e-3, gamma * (1.0 - (double)nr / n)));
+    // direction features (inputs of the learned start, exported with P)
+    if ((st = lk_malloc(ctx, (void**)&P->feat, (size_t)2 * nr * sizeof(float))) != LAKER_OK) return st;
+    k_dir_features<<<gsz(nr), 256, 0, s>>>(nr, tmpv, M, P->feat);
+    LK_LAUNCHED(ctx);
     CccpState h{};
     h.c = 1.0;
-    LK_CUDA(ctx, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     LK_CUDA(ctx, cudaMemsetAsync(D, 0, NP * sizeof(double), s));
+    if (net) {
+        // Sigma_0 = c0 I + U diag(D0) U^T from the set network, scaled to tr = n
+        const float *logc = nullptr, *logD = nullptr;
+        if ((st = setnet_predict(ctx, net, n, Xpts, nr, P->feat, &logc, &logD)) != LAKER_OK) return st;
+        std::vector<float> hD((size_t)nr);
+        float hc = 0.f;
+        LK_CUDA(ctx, cudaMemcpyAsync(&hc, logc, sizeof(float), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaMemcpyAsync(hD.data(), logD, sizeof(float) * nr, cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        std::vector<double> D0((size_t)nr);
+        double tr = (double)n * std::exp((double)hc);
+        for (int k = 0; k < nr; ++k) {
+            D0[(size_t)k] = std::exp(std::min(50.0, (double)hD[(size_t)k]));   // M_kk = 1
+            tr += D0[(size_t)k];
+        }
+        const double f = (double)n / tr;
+        h.c = std::exp((double)hc) * f;
+        for (double& v : D0) v *= f;
+        if (!(h.c > 0.0) || !std::isfinite(h.c)) return set_error(ctx, LAKER_ERR_NONFINITE, "learned start: bad c");
+        LK_CUDA(ctx, cudaMemcpyAsync(D, D0.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, s));
+    }
+    LK_CUDA(ctx, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     int* dstatus = &dst->status;
-    for (int it = 0; it < max_iter; ++it) {
+    const int cccp_iters = (net && mode == 1) ? 0 : max_iter;
+    for (int it = 0; it < cccp_iters; ++it) {
         k_cccp_form<<<gsz((int64_t)2 * NP * NP), 256, 0, s>>>(NP, nr, M, D, dst, A);
         LK_LAUNCHED(ctx);
         for (int jb = 0; jb < ncb; ++jb) {

@@ -81,6 +81,7 @@ struct laker_precond {
     float* UT32 = nullptr;    // n_r x ldu, U transposed (float32 applies)
     double* dinv = nullptr;   // Jacobi: 1/diag(A)
     bool use32 = false;       // apply in float32 (mixed solves)
+    float* feat = nullptr;    // n_r x 2: [log |u_k|, sum_j M_kj^2] (inputs of the learned start)
 };
 
 // ---- error plumbing ------------------------------------------------------
@@ -116,7 +117,8 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
 // laker_fit.cu
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
                       double gamma, double rho, double eps, int max_iter, double tol,
-                      laker_precond* P, laker_fit_info* info);
+                      laker_precond* P, laker_fit_info* info,
+                      laker_setnet* net = nullptr, const float* X = nullptr, int mode = 0);
 // laker_map.cu
 laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
                       const double* alpha, double* out);
@@ -126,6 +128,10 @@ void mf_release(laker_op* op);
 laker_status mf_status(laker_ctx* ctx, const laker_op* op);
 laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+// laker_setnet.cu
+laker_status setnet_predict(laker_ctx* ctx, laker_setnet* s, int64_t n, const float* X, int nr, const float* F,
+                            const float** logc, const float** logD);
+int setnet_in_dim(const laker_setnet* s);
 // laker_batch.cu
 laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items, double tol, int max_iter,
                                int refine_every, laker_solve_info* infos, double* done_ms);

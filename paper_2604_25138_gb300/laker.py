@@ -58,6 +58,7 @@ def library() -> ctypes.CDLL:
     lib = ctypes.CDLL(LIB_PATH)
     vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     pvp = ctypes.POINTER(ctypes.c_void_p)
+    pi32 = ctypes.POINTER(ctypes.c_int)
     sig = {
         "laker_create": (i32, [pvp, i32, vp]),
         "laker_destroy": (i32, [vp]),
@@ -68,6 +69,19 @@ def library() -> ctypes.CDLL:
         "laker_op_destroy": (i32, [vp]),
         "laker_pcg_solve_batched": (i32, [vp, i32, ctypes.POINTER(BatchItem), f64, i32, i32,
                                           ctypes.POINTER(SolveInfo), ctypes.POINTER(f64)]),
+        "laker_setnet_create": (i32, [vp, i32, i32, i32, ctypes.c_uint64, pvp]),
+        "laker_setnet_destroy": (i32, [vp]),
+        "laker_setnet_num_params": (i64, [vp]),
+        "laker_setnet_get_params": (i32, [vp, vp, vp]),
+        "laker_setnet_set_params": (i32, [vp, vp, vp]),
+        "laker_setnet_point_features": (i32, [vp, i64, i32, vp, vp, vp, vp]),
+        "laker_setnet_forward": (i32, [vp, vp, i32, vp, pi32, vp, pi32, vp, vp]),
+        "laker_setnet_gradient": (i32, [vp, vp, i32, vp, pi32, vp, pi32, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]),
+        "laker_setnet_train_step": (i32, [vp, vp, i32, vp, pi32, vp, pi32, vp, vp, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_float)]),
+        "laker_precond_direction_features": (i32, [vp, vp, vp]),
+        "laker_fit_preconditioner_learned": (i32, [vp, vp, vp, i32, f64, f64, f64, i32, f64, vp, vp, i32, pvp,
+                                                   ctypes.POINTER(FitInfo)]),
         "laker_op_matvec": (i32, [vp, vp, vp, vp]),
         "laker_op_matvec_fp64": (i32, [vp, vp, vp, vp]),
         "laker_op_time_operator": (i32, [vp, vp, vp, i32, ctypes.POINTER(f64)]),
@@ -225,6 +239,135 @@ def laker_fit_preconditioner(ctx: Context, op: Operator, Z: torch.Tensor, gamma:
     with ctx:
         ctx.check(library().laker_fit_preconditioner(ctx.handle, op.handle, _ptr(Z, "Z", op.n * n_r), n_r, gamma,
                                                      rho, eps, max_iter, tol, ctypes.byref(h), ctypes.byref(info)))
+    d = {f: getattr(info, f) for f, _ in FitInfo._fields_}
+    return Preconditioner(ctx, h, n, n_r, d)
+
+
+class SetNet:
+    """Handle of the learned set-to-parameters network (device weights)."""
+
+    def __init__(self, ctx: Context, in_dim: int, hidden: int = 256, dir_hidden: int = 64, seed: int = 0):
+        self.ctx = ctx
+        self.in_dim, self.hidden, self.dir_hidden = in_dim, hidden, dir_hidden
+        h = ctypes.c_void_p()
+        with ctx:
+            ctx.check(library().laker_setnet_create(ctx.handle, in_dim, hidden, dir_hidden, seed, ctypes.byref(h)))
+        self.handle = h
+
+    def num_params(self) -> int:
+        return int(library().laker_setnet_num_params(self.handle))
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params(), dtype=np.float32)
+        with self.ctx:
+            self.ctx.check(library().laker_setnet_get_params(self.ctx.handle, self.handle,
+                                                             out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, theta):
+        import numpy as np
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.num_params():
+            raise ValueError("parameter vector has the wrong size")
+        with self.ctx:
+            self.ctx.check(library().laker_setnet_set_params(self.ctx.handle, self.handle,
+                                                             t.ctypes.data_as(ctypes.c_void_p)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().laker_setnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _offsets(counts):
+    arr = (ctypes.c_int * (len(counts) + 1))()
+    s = 0
+    arr[0] = 0
+    for k, c in enumerate(counts):
+        s += int(c)
+        arr[k + 1] = s
+    return arr
+
+
+def _f32(t: torch.Tensor, name: str, numel: int | None = None):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def laker_setnet_point_features(ctx: Context, loc: torch.Tensor, Q: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    n, d = Q.shape
+    X = torch.empty((n, d + 3), dtype=torch.float32, device=Q.device)
+    with ctx:
+        ctx.check(library().laker_setnet_point_features(ctx.handle, n, d, _ptr(loc, "loc", 2 * n), _ptr(Q, "Q"),
+                                                        _ptr(y, "y", n), _f32(X, "X")))
+    return X
+
+
+def laker_setnet_forward(ctx: Context, net: SetNet, X: torch.Tensor, n_points, F: torch.Tensor, n_dirs):
+    """X: concatenated point features, n_points per instance; F: concatenated
+    direction features, n_dirs per instance.  Returns (log c, log D)."""
+    B = len(n_points)
+    po, ko = _offsets(n_points), _offsets(n_dirs)
+    logc = torch.empty(B, dtype=torch.float32, device=X.device)
+    logD = torch.empty(max(1, ko[B]), dtype=torch.float32, device=X.device)
+    with ctx:
+        ctx.check(library().laker_setnet_forward(ctx.handle, net.handle, B, _f32(X, "X"), po, _f32(F, "F"), ko,
+                                                 _f32(logc, "logc"), _f32(logD, "logD")))
+    return logc, logD[:ko[B]]
+
+
+def laker_setnet_gradient(ctx: Context, net: SetNet, X, n_points, F, n_dirs, tc: torch.Tensor, tD: torch.Tensor):
+    B = len(n_points)
+    po, ko = _offsets(n_points), _offsets(n_dirs)
+    grad = torch.empty(net.num_params(), dtype=torch.float32, device=X.device)
+    loss = ctypes.c_float()
+    with ctx:
+        ctx.check(library().laker_setnet_gradient(ctx.handle, net.handle, B, _f32(X, "X"), po, _f32(F, "F"), ko,
+                                                  _f32(tc, "tc", B), _f32(tD, "tD", ko[B]), _f32(grad, "grad"),
+                                                  ctypes.byref(loss)))
+    return grad, float(loss.value)
+
+
+def laker_setnet_train_step(ctx: Context, net: SetNet, X, n_points, F, n_dirs, tc, tD, lr: float) -> float:
+    B = len(n_points)
+    po, ko = _offsets(n_points), _offsets(n_dirs)
+    loss = ctypes.c_float()
+    with ctx:
+        ctx.check(library().laker_setnet_train_step(ctx.handle, net.handle, B, _f32(X, "X"), po, _f32(F, "F"), ko,
+                                                    _f32(tc, "tc", B), _f32(tD, "tD", ko[B]), lr, ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def laker_precond_direction_features(ctx: Context, P: Preconditioner) -> torch.Tensor:
+    F = torch.empty((P.n_r, 2), dtype=torch.float32, device="cuda")
+    with ctx:
+        ctx.check(library().laker_precond_direction_features(ctx.handle, P.handle, _f32(F, "F")))
+    return F
+
+
+def laker_fit_preconditioner_learned(ctx: Context, op: Operator, Z: torch.Tensor, net: SetNet, X: torch.Tensor,
+                                     mode: int = 0, gamma: float = 0.1, rho: float = -1.0, eps: float = 1e-8,
+                                     max_iter: int = 200, tol: float = 1e-10) -> Preconditioner:
+    """mode 0: CCCP iterations started from the network's prediction; mode 1:
+    the prediction is used as Sigma_* directly."""
+    n, n_r = Z.shape
+    info = FitInfo()
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_fit_preconditioner_learned(ctx.handle, op.handle, _ptr(Z, "Z", op.n * n_r), n_r,
+                                                             gamma, rho, eps, max_iter, tol, net.handle,
+                                                             _f32(X, "X", n * net.in_dim), mode, ctypes.byref(h),
+                                                             ctypes.byref(info)))
     d = {f: getattr(info, f) for f, _ in FitInfo._fields_}
     return Preconditioner(ctx, h, n, n_r, d)
 
