@@ -404,6 +404,86 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_learned(args):
+    """Learned-preconditioner workload (scaled down for the time budget): the
+    set network is trained on the method's own CCCP fits of seeded training
+    instances (n uniform in [1024, 4096], d = 32, lambda log-uniform in
+    [1e-5, 1e-2], 1-8 Tx), then held-out instances of the same distribution and
+    a few at n = 16384 are solved with: the cold CCCP fit, the warm-started fit,
+    the prediction used as Sigma_* (with CCCP as the fallback when it needs more
+    than 1.2x CCCP's PCG iterations), Jacobi and no preconditioner."""
+    import torch
+
+    from paper_2604_25138_gb300 import build
+    from paper_2604_25138_gb300 import laker as L
+    from paper_2604_25138_gb300 import learned
+
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = L.Context(0)
+    rng = np.random.default_rng(5005)
+
+    def draw(k0, count, n_fixed=None):
+        out = []
+        for k in range(count):
+            n = n_fixed or int(rng.integers(1024, 4097))
+            lam = float(10 ** rng.uniform(-5, -2))
+            out.append(synth.make_instance(n, 32, lam, n_tx=int(rng.integers(1, 9)), seed=k0 + k, grid=2))
+        return out
+
+    n_train, n_test, n_big = args.learned_train, args.learned_test, args.learned_big
+    t0 = time.perf_counter()
+    train_set = [learned.fit_example(ctx, inst, seed=inst.seed) for inst in draw(50000, n_train)]
+    gen_s = time.perf_counter() - t0
+    net = L.SetNet(ctx, 32 + 3, 256, 64, seed=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = learned.train(ctx, net, train_set, steps=args.learned_steps, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    rows = []
+    for inst in draw(70000, n_test) + draw(80000, n_big, n_fixed=16384):
+        r = learned.compare(ctx, net, inst, seed=inst.seed)
+        r["n"] = inst.n
+        rows.append(r)
+
+    def summary(sel):
+        out = {}
+        for k in ("cccp", "warm", "learned", "jacobi", "none"):
+            it = [r[k]["iterations"] for r in sel]
+            fit = [r[k]["fit_s"] for r in sel]
+            sol = [r[k]["solve_s"] for r in sel]
+            conv = sum(int(r[k]["converged"] == 1) for r in sel)
+            out[k] = {"pcg_iterations_mean": float(np.mean(it)), "fit_ms_mean": 1e3 * float(np.mean(fit)),
+                      "solve_ms_mean": 1e3 * float(np.mean(sol)), "converged": conv,
+                      "solves_per_s": len(sel) / float(np.sum(fit) + np.sum(sol))}
+            if k in ("cccp", "warm"):
+                out[k]["cccp_iterations_mean"] = float(np.mean([r[k]["cccp_iterations"] for r in sel]))
+        # learned with the fallback: CCCP's time and iterations are charged when it falls back
+        fb = [r["fallback"] for r in sel]
+        t = [(r["learned"]["fit_s"] + r["learned"]["solve_s"]) + ((r["cccp"]["fit_s"] + r["cccp"]["solve_s"])
+                                                                 if r["fallback"] else 0.0) for r in sel]
+        out["learned_with_fallback"] = {"fallback_rate": float(np.mean(fb)), "solves_per_s": len(sel) / float(np.sum(t))}
+        return out
+
+    small = [r for r in rows if r["n"] < 16384]
+    big = [r for r in rows if r["n"] == 16384]
+    line = {
+        "metric": "end-to-end solves/s with the learned preconditioner (fit or prediction + mixed PCG to 1e-6)",
+        "value": summary(small)["learned_with_fallback"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": len(small), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 net, f32 operator, f64 scalars", "data": "synthetic",
+        "config": {"workload": "learned preconditioner: train on %d CCCP fits (n in [1024, 4096], d = 32, lambda "
+                               "log-uniform in [1e-5, 1e-2], 1-8 Tx), test on %d held-out + %d at n = 16384"
+                               % (n_train, n_test, n_big),
+                   "train_examples_s": gen_s, "train_s": train_s, "train_steps": args.learned_steps,
+                   "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:]))},
+        "held_out": summary(small),
+        "n16384": summary(big) if big else None,
+    }
+    print(json.dumps(line))
+
+
 # ---------------------------------------------------------------------------
 # The FP64 oracle on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
@@ -485,13 +565,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iterations", type=int, default=1500)
     ap.add_argument("--ref-cccp-iterations", type=int, default=30)
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
-                    help="single: the n=16384 instance (the headline line); batched: 256 instances")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned"],
+                    help="single: the n=16384 instance (the headline line); batched: 256 instances; "
+                         "learned: the set-network preconditioner")
+    ap.add_argument("--learned-train", type=int, default=256)
+    ap.add_argument("--learned-test", type=int, default=32)
+    ap.add_argument("--learned-big", type=int, default=4)
+    ap.add_argument("--learned-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 
