@@ -46,6 +46,8 @@ def main(argv=None):
         return
     Z = dev(synth.directions(a.n, synth.default_num_directions(a.n), a.seed))
     P = L.laker_fit_preconditioner(ctx, op, Z)
+    torch.cuda.synchronize()
+    print(f"launches before solve {ctx.launches()}", flush=True)
     if a.case == "solve":
         alpha, info = L.laker_pcg_solve(ctx, op, P, dev(inst.y), 1e-6, max_iter=20000, refine_every=20)
         print(f"solve n={a.n} {a.precision}: {info}")
