@@ -37,7 +37,8 @@ struct BInst {
     int64_t ldu;
     double cinv;
     const void* UT;        // n_r x ldu
-    const void* W;         // n x n_r
+    const void* W;         // n x ldw
+    int ldw;
     const double* dinv;
     const double* y;
     double* alpha;
@@ -199,7 +200,7 @@ __device__ void ph_precond(const BArgs& a, double* red, double* ts) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) wv[q][c] = (q < nrow) ? W[(i + q) * I.n_r + k + 32 * c] : PT(0);
+                        for (int c = 0; c < 4; ++c) wv[q][c] = (q < nrow) ? W[(i + q) * I.ldw + k + 32 * c] : PT(0);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const double tk = ts[k + 32 * c];
@@ -211,7 +212,7 @@ __device__ void ph_precond(const BArgs& a, double* red, double* ts) {
                     const double tk = ts[k];
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (q < nrow) s[q] = fma((double)W[(i + q) * I.n_r + k], tk, s[q]);
+                        if (q < nrow) s[q] = fma((double)W[(i + q) * I.ldw + k], tk, s[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) s[q] = lk::warp_sum(s[q]);
@@ -700,6 +701,7 @@ laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item
             I.cinv = P->cinvsqrt;
             I.UT = fp64_prec ? (const void*)P->UT64 : (const void*)P->UT32;
             I.W = fp64_prec ? (const void*)P->W64 : (const void*)P->W32;
+            I.ldw = fp64_prec ? P->n_r : P->ldw;
             I.t = tv + offt;
             offt += P->n_r;
         }

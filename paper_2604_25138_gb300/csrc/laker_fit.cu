@@ -527,11 +527,14 @@ __global__ void k_diag_max(int m, const double* __restrict__ S, double* out) {
     }
 }
 
-// W[i][k] = float(Ut[i][k] phi_k)
-__global__ void k_scale_cols_to_float(int64_t n, int nr, const double* __restrict__ Ut, const double* __restrict__ phi,
-                                      float* __restrict__ W) {
+// W[i][k] = float(Ut[i][k] phi_k) with row pitch ldw (zeros in the padding)
+__global__ void k_scale_cols_to_float(int64_t n, int nr, int ldw, const double* __restrict__ Ut,
+                                      const double* __restrict__ phi, float* __restrict__ W) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < n * nr) W[idx] = (float)(Ut[idx] * phi[idx % nr]);
+    if (idx >= n * ldw) return;
+    const int64_t i = idx / ldw;
+    const int k = (int)(idx % ldw);
+    W[idx] = (k < nr) ? (float)(Ut[i * nr + k] * phi[k]) : 0.f;
 }
 
 unsigned gsz(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b); }
@@ -733,10 +736,11 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         if ((st = gemm<float>(ctx, false, false, n, nr, nr, U32, nr, C32, nr, 0.0, nullptr, 0, Ut, nr)) != LAKER_OK)
             return st;
         if ((st = lk_malloc(ctx, (void**)&P->UT32, (size_t)nr * P->ldu * sizeof(float))) != LAKER_OK) return st;
-        if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        P->ldw = (nr + 3) / 4 * 4;
+        if ((st = lk_malloc(ctx, (void**)&P->W32, (size_t)n * P->ldw * sizeof(float))) != LAKER_OK) return st;
         k_transpose<float><<<tg, tb, 0, s>>>(n, nr, P->ldu, Ut, P->UT32);
         LK_LAUNCHED(ctx);
-        k_scale_cols_to_float<<<gsz(n * nr), 256, 0, s>>>(n, nr, Ut, phi, P->W32);
+        k_scale_cols_to_float<<<gsz(n * P->ldw), 256, 0, s>>>(n, nr, P->ldw, Ut, phi, P->W32);
         LK_LAUNCHED(ctx);
         LK_CUDA(ctx, cudaStreamSynchronize(s));
         for (void* ptr : {(void*)C32, (void*)U32, (void*)phi, (void*)Ut}) cudaFree(ptr);

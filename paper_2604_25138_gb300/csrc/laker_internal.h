@@ -75,7 +75,8 @@ struct laker_precond {
     double* D = nullptr;      // n_r
     double* U64 = nullptr;    // n x n_r, unit columns u_bar_k
     double* W64 = nullptr;    // n x n_r, W = U B with P = c^{-1/2} I + W U^T
-    float* W32 = nullptr;
+    float* W32 = nullptr;     // n x ldw (zero padding), float32 applies
+    int ldw = 0;              // row pitch of W32: n_r rounded up to 4
     int64_t ldu = 0;          // row pitch of UT (n rounded up to 4)
     double* UT64 = nullptr;   // n_r x ldu, U transposed (float64 applies)
     float* UT32 = nullptr;    // n_r x ldu, U transposed (float32 applies)

@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <vector>
 #include <cstring>
 
 #include "laker_device.cuh"
@@ -265,7 +266,8 @@ __device__ __forceinline__ void mf_tile_epilogue(uint32_t tcol, float2* acc, con
 // Epilogue warp (quadrant q, part h) owns lanes 32q..32q+31 and columns
 // 32h..32h+31: it accumulates the block-I row sums over its lanes in
 // registers for the whole segment, and writes the block-J sums of an
-// off-diagonal tile to colpart[(x * MF_EPW + h) * 128 + j].  At the end of a
+// off-diagonal tile to colpart[(x * 128 + j) * MF_EPW + h] (the four parts of a
+// column are one 16-byte load for the finishing kernel).  At the end of a
 // segment the row sums are reduced over the lanes and stored to
 // rowpart[((I * slots + slot) * 4 + q) * 128 + i].
 template <int DPAD>
@@ -431,7 +433,7 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(&S->tempty[accb]);
             if (!diag)
-                colpart[((t0 + it) * MF_EPW + h) * MF_B + q * 32 + lane] = (sJ[0].x + sJ[0].y) + (sJ[1].x + sJ[1].y);
+                colpart[((t0 + it) * MF_B + q * 32 + lane) * MF_EPW + h] = (sJ[0].x + sJ[0].y) + (sJ[1].x + sJ[1].y);
             I = In;
             k = kn;
         }
@@ -460,58 +462,65 @@ __global__ void k_mf_prep(int64_t n, int64_t npad, const double* __restrict__ pi
 }
 
 // w_i = lambda p_i + (block row I's segment partials over slots and lane
-// quadrants) + (column sums of the off-diagonal tiles (I', I)).  One CTA per
-// block row I, 4 x 128 threads: group t / 128 takes the distances
-// kk = 1 + group, 5 + group, ...; the groups are added in a fixed order.
-// p^T w -> delta in the last CTA.
-constexpr int MF_FIN_GROUPS = 4;
-__global__ void __launch_bounds__(MF_FIN_GROUPS * MF_B)
+// quadrants) + (column sums of the off-diagonal tiles (I', I)).  CTA (I, cq)
+// takes the 32 columns 32cq..32cq+31 of block row I with 16 groups of 32
+// threads: group g adds the distances kk = 1 + g, 17 + g, ... and a share of
+// the row partials; the groups are added in a fixed order.  p^T w -> delta in
+// the last CTA.
+constexpr int MF_FIN_COLS = 32;
+static_assert(MF_EPW == 4, "the finishing kernel reads the four epilogue parts of a column as one float4");
+constexpr int MF_FIN_GROUPS = 16;
+__global__ void __launch_bounds__(MF_FIN_GROUPS * MF_FIN_COLS)
 k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ rowpart,
-            const float* __restrict__ colpart, const double* __restrict__ p, double* __restrict__ w, PcgScalars* sc,
-            double* __restrict__ partials, const int* err) {
+            const float* __restrict__ colpart, const int* __restrict__ nslots, const double* __restrict__ p,
+            double* __restrict__ w, PcgScalars* sc, double* __restrict__ partials, const int* err) {
     if (sc != nullptr && *(volatile const int*)&sc->converged) return;
-    __shared__ double red[MF_FIN_GROUPS * MF_B / 32];
-    __shared__ float gsum[MF_FIN_GROUPS][MF_B];
-    const int I = blockIdx.x, c = threadIdx.x % MF_B, grp = threadIdx.x / MF_B;
+    __shared__ double red[MF_FIN_GROUPS * MF_FIN_COLS / 32];
+    __shared__ float gsum[MF_FIN_GROUPS][MF_FIN_COLS];
+    const int I = blockIdx.x;
+    const int c = blockIdx.y * MF_FIN_COLS + (threadIdx.x % MF_FIN_COLS);
+    const int grp = threadIdx.x / MF_FIN_COLS;
+    // row partials: the (slot, quadrant) entries are spread over the groups
     float s = 0.f;
-    if (grp == 0) {
-        const int64_t xs = mf_row_start(I, sch);
-        const int g0 = mf_owner(xs, sch), g1 = mf_owner(xs + mf_row_len(I, sch) - 1, sch);
-        for (int slot = 0; slot <= g1 - g0; ++slot)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s += rowpart[(((int64_t)I * sch.slots + slot) * 4 + q) * MF_B + c];
+    {
+        const int nslot = nslots[I];   // CTAs that own a segment of block row I
+        for (int e = grp; e < 4 * nslot; e += MF_FIN_GROUPS)
+            s += __ldg(rowpart + (((int64_t)I * sch.slots + e / 4) * 4 + (e % 4)) * MF_B + c);
     }
+    // column sums of the tiles (I - kk, I): four independent 16-byte loads in flight
     float t[2] = {0.f, 0.f};
-    int u = 0;
-    for (int kk = 1 + grp; kk <= sch.base; kk += MF_FIN_GROUPS, u ^= 1) {
-        int Ip = I - kk;
-        if (Ip < 0) Ip += sch.nb;
-        if (kk < mf_row_len(Ip, sch)) {
-            const int64_t x = mf_row_start(Ip, sch) + kk;
-            const float* cp = colpart + x * MF_EPW * MF_B + c;
-            float v = 0.f;
+    const float4* cp4 = reinterpret_cast<const float4*>(colpart);
+    for (int kb = 1 + grp; kb <= sch.base; kb += 4 * MF_FIN_GROUPS) {
+        float4 v[4];
 #pragma unroll
-            for (int h = 0; h < MF_EPW; ++h) v += cp[h * MF_B];
-            t[u] += v;
+        for (int u = 0; u < 4; ++u) {
+            const int kk = kb + u * MF_FIN_GROUPS;
+            int Ip = I - kk;
+            if (Ip < 0) Ip += sch.nb;
+            const bool ok = kk <= sch.base && kk < mf_row_len(Ip, sch);
+            v[u] = ok ? __ldg(cp4 + (mf_row_start(Ip, sch) + kk) * MF_B + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u & 1] += (v[u].x + v[u].y) + (v[u].z + v[u].w);
     }
-    gsum[grp][c] = s + (t[0] + t[1]);
+    gsum[grp][threadIdx.x % MF_FIN_COLS] = s + (t[0] + t[1]);
     __syncthreads();
     const int64_t i = (int64_t)I * MF_B + c;
     double pw = 0.0;
     if (grp == 0 && i < n) {
         double tot = 0.0;
 #pragma unroll
-        for (int gq = 0; gq < MF_FIN_GROUPS; ++gq) tot += (double)gsum[gq][c];
+        for (int gq = 0; gq < MF_FIN_GROUPS; ++gq) tot += (double)gsum[gq][threadIdx.x];
         const double wi = fma(lambda, p[i], tot);
         w[i] = wi;
         pw = p[i] * wi;
     }
     if (sc == nullptr) return;
     pw = lk::block_sum(pw, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = pw;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) partials[bid] = pw;
     if (lk::last_block(&sc->ticket[0])) {
-        const double pAp = lk::sum_partials(partials, gridDim.x, red);
+        const double pAp = lk::sum_partials(partials, gridDim.x * gridDim.y, red);
         if (threadIdx.x == 0) {
             sc->pAp = pAp;
             if (*(volatile const int*)err != 0 || !(pAp > 0.0) || !isfinite(pAp)) {
@@ -557,6 +566,7 @@ struct MfWork {
     float* rowpart = nullptr;   // segment row sums (see k_mf_bf16x3)
     float* colpart = nullptr;   // column sums of off-diagonal tiles
     int* err = nullptr;         // device error word
+    int* nslots = nullptr;      // per block row: number of CTAs owning a segment of it
     MfSched sch;
 };
 
@@ -608,6 +618,15 @@ laker_status mf_prepare(laker_ctx* ctx, laker_op* op) {
         return st;
     }
     if ((st = lk_malloc(ctx, (void**)&wk->err, sizeof(int))) != LAKER_OK) { mf_release_work(wk); return st; }
+    {
+        std::vector<int> ns((size_t)sc.nb);
+        for (int I = 0; I < sc.nb; ++I) {
+            const int64_t x0 = mf_row_start(I, sc);
+            ns[(size_t)I] = mf_owner(x0 + mf_row_len(I, sc) - 1, sc) - mf_owner(x0, sc) + 1;
+        }
+        if ((st = lk_malloc(ctx, (void**)&wk->nslots, sizeof(int) * sc.nb)) != LAKER_OK) { mf_release_work(wk); return st; }
+        LK_CUDA(ctx, cudaMemcpy(wk->nslots, ns.data(), sizeof(int) * sc.nb, cudaMemcpyHostToDevice));
+    }
     LK_CUDA(ctx, cudaMemsetAsync(wk->err, 0, sizeof(int), ctx->stream));
     const cuuint64_t dims[2] = {(cuuint64_t)op->dpad, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)op->dpad * 2};
@@ -642,6 +661,7 @@ static void mf_release_work(MfWork* wk) {
     cudaFree(wk->rowpart);
     cudaFree(wk->colpart);
     cudaFree(wk->err);
+    cudaFree(wk->nslots);
     delete wk;
 }
 
@@ -670,7 +690,7 @@ laker_status mf_matvec_launch(laker_ctx* ctx, const laker_op* op, const double* 
     LK_LAUNCHED(ctx);
     laker_status st = mf_launch_main(ctx, op, wk, sc);
     if (st != LAKER_OK) return st;
-    k_mf_finish<<<wk->sch.nb, MF_FIN_GROUPS * MF_B, 0, ctx->stream>>>(n, wk->sch, op->lambda, wk->rowpart, wk->colpart, p, w, sc, partials,
+    k_mf_finish<<<dim3(wk->sch.nb, MF_B / MF_FIN_COLS), MF_FIN_GROUPS * MF_FIN_COLS, 0, ctx->stream>>>(n, wk->sch, op->lambda, wk->rowpart, wk->colpart, wk->nslots, p, w, sc, partials,
                                              wk->err);
     LK_LAUNCHED(ctx);
     return LAKER_OK;

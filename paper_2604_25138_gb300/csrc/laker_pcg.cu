@@ -241,6 +241,7 @@ __device__ __forceinline__ void row_range(int64_t n, int64_t& r0, int64_t& r1) {
 struct PrecView {
     int kind;
     int n_r;
+    int ldw;          // row pitch of W (n_r rounded up to 4 for float32 W, n_r for float64)
     int64_t ldu;
     double cinv;
     const void* UT;   // n_r x ldu, U transposed
@@ -368,34 +369,68 @@ __device__ __forceinline__ double dot_vec(const double2& u, const double* r) {
     return fma(u.x, rr.x, u.y * rr.y);
 }
 
+template <typename PT> __device__ __forceinline__ void load_r(const double* r, int64_t e, PT* rv);
+template <> __device__ __forceinline__ void load_r<float>(const double* r, int64_t e, float* rv) {
+    const double2 a = *reinterpret_cast<const double2*>(r + e), b = *reinterpret_cast<const double2*>(r + e + 2);
+    rv[0] = (float)a.x; rv[1] = (float)a.y; rv[2] = (float)b.x; rv[3] = (float)b.y;
+}
+template <> __device__ __forceinline__ void load_r<double>(const double* r, int64_t e, double* rv) {
+    const double2 a = *reinterpret_cast<const double2*>(r + e);
+    rv[0] = a.x; rv[1] = a.y;
+}
+__device__ __forceinline__ float dot_v(const float4& u, const float* rv) {
+    return fmaf(u.x, rv[0], fmaf(u.y, rv[1], fmaf(u.z, rv[2], u.w * rv[3])));
+}
+__device__ __forceinline__ double dot_v(const double2& u, const double* rv) { return fma(u.x, rv[0], u.y * rv[1]); }
+
+// UTR: t_k = sum_i U_ik r_i for four directions k0..k0+3 per block: every load
+// of r serves the four rows of U^T (padded pitch ldu, zeros past n), 16-byte
+// loads, two steps in flight; each block reduces its four sums in a fixed order.
 template <typename PT>
 __global__ void __launch_bounds__(256)
 k_utr(int64_t n, PrecView pv, const double* __restrict__ r, PT* __restrict__ t, const PcgScalars* sc, int gate) {
     if (gated_out(sc, gate)) return;
-    __shared__ PT red[8];
+    __shared__ PT red[4][8];
     constexpr int VN = UtrVec<PT>::N;
     using V = typename UtrVec<PT>::type;
-    const int k = blockIdx.x;
-    const V* u = reinterpret_cast<const V*>((const PT*)pv.UT + (int64_t)k * pv.ldu);
+    const int k0 = blockIdx.x * 4;
+    const int nk = min(4, pv.n_r - k0);
+    const V* u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = reinterpret_cast<const V*>((const PT*)pv.UT + (int64_t)(k0 + (q < nk ? q : 0)) * pv.ldu);
     const int64_t nfull = n / VN;                 // vectors entirely inside [0, n)
-    PT a0 = PT(0), a1 = PT(0);
+    PT a[4] = {PT(0), PT(0), PT(0), PT(0)}, b[4] = {PT(0), PT(0), PT(0), PT(0)};
     int64_t v = threadIdx.x;
     for (; v + 256 < nfull; v += 512) {
-        const V u0 = __ldg(u + v), u1 = __ldg(u + v + 256);
-        a0 += dot_vec(u0, r + v * VN);
-        a1 += dot_vec(u1, r + (v + 256) * VN);
+        PT ra[VN], rb[VN];
+        load_r<PT>(r, v * VN, ra);
+        load_r<PT>(r, (v + 256) * VN, rb);
+        V ua[4], ub[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { ua[q] = __ldg(u[q] + v); ub[q] = __ldg(u[q] + v + 256); }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { a[q] += dot_v(ua[q], ra); b[q] += dot_v(ub[q], rb); }
     }
-    for (; v < nfull; v += 256) a0 += dot_vec(__ldg(u + v), r + v * VN);
-    const PT* us = (const PT*)pv.UT + (int64_t)k * pv.ldu;
-    for (int64_t i = nfull * VN + threadIdx.x; i < n; i += 256) a1 += us[i] * (PT)r[i];
-    PT a = lk::warp_sum(a0 + a1);
+    for (; v < nfull; v += 256) {
+        PT ra[VN];
+        load_r<PT>(r, v * VN, ra);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] += dot_v(__ldg(u[q] + v), ra);
+    }
+    for (int64_t i = nfull * VN + threadIdx.x; i < n; i += 256)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] += reinterpret_cast<const PT*>(u[q])[i] * (PT)r[i];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = a;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const PT s = lk::warp_sum(a[q] + b[q]);
+        if (lane == 0) red[q][wid] = s;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nk) {
         PT s = PT(0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        t[k] = s;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        t[k0 + threadIdx.x] = s;
     }
 }
 
@@ -407,11 +442,56 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
           double* __restrict__ partials, PrecView pv, const PT* __restrict__ t, int gate) {
     if (gated_out(sc, gate)) return;
     __shared__ double red[VEC_THREADS / 32];
-    __shared__ PT ts[LK_MAX_NR];
+    __shared__ __align__(16) PT ts[LK_MAX_NR];
     int64_t r0, r1;
     row_range(n, r0, r1);
     double rz = 0.0;
-    if (pv.kind == PRECOND_CCCP) {
+    if (pv.kind == PRECOND_CCCP && sizeof(PT) == 4) {
+        // float32 W with a 16-byte row pitch: four rows per warp, float4 loads
+        for (int k = threadIdx.x; k < pv.ldw; k += blockDim.x) ts[k] = (k < pv.n_r) ? __ldcg(t + k) : PT(0);
+        __syncthreads();
+        const float4* W4 = reinterpret_cast<const float4*>(pv.W);
+        const float4* t4 = reinterpret_cast<const float4*>(ts);
+        const int nk4 = pv.ldw / 4;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int64_t i = r0 + 4 * wid; i < r1; i += 4 * nw) {
+            const int nrow = (r1 - i < 4) ? (int)(r1 - i) : 4;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            int k4 = lane;
+            for (; k4 + 96 < nk4; k4 += 128) {   // 16 independent 16-byte loads in flight
+                float4 w[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        w[q][u] = (q < nrow) ? __ldg(W4 + (i + q) * nk4 + k4 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 tk = t4[k4 + 32 * u];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc[q] = fmaf(w[q][u].x, tk.x, fmaf(w[q][u].y, tk.y, fmaf(w[q][u].z, tk.z, fmaf(w[q][u].w, tk.w, acc[q]))));
+                }
+            }
+            for (; k4 < nk4; k4 += 32) {
+                const float4 tk = t4[k4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 w = (q < nrow) ? __ldg(W4 + (i + q) * nk4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    acc[q] = fmaf(w.x, tk.x, fmaf(w.y, tk.y, fmaf(w.z, tk.z, fmaf(w.w, tk.w, acc[q]))));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float a = lk::warp_sum(acc[q]);
+                if (lane == 0 && q < nrow) {
+                    const double zi = fma(pv.cinv, r[i + q], (double)a);
+                    z[i + q] = zi;
+                    rz = fma(r[i + q], zi, rz);
+                }
+            }
+        }
+    } else if (pv.kind == PRECOND_CCCP) {
         for (int k = threadIdx.x; k < pv.n_r; k += blockDim.x) ts[k] = __ldcg(t + k);
         __syncthreads();
         const PT* W = (const PT*)pv.W;
@@ -503,8 +583,8 @@ int vec_blocks_for(const laker_ctx* ctx, int64_t n) {
 }
 // The preconditioner apply streams W (n x n_r): many blocks.
 int pre_blocks_for(const laker_ctx* ctx, int64_t n) {
-    int64_t b = (n + 15) / 16;
-    b = std::min<int64_t>(b, 2 * ctx->num_sms);
+    int64_t b = (n + 31) / 32;                     // >= 32 rows: every warp has four rows
+    b = std::min<int64_t>(b, 8 * ctx->num_sms);
     return (int)std::max<int64_t>(1, b);
 }
 int mv_blocks_for(const laker_ctx* ctx, int64_t n) {
@@ -559,6 +639,7 @@ PrecView make_view(const laker_precond* P, bool use32) {
     v.cinv = P->cinvsqrt;
     v.UT = use32 ? (const void*)P->UT32 : (const void*)P->UT64;
     v.W = use32 ? (const void*)P->W32 : (const void*)P->W64;
+    v.ldw = use32 ? P->ldw : P->n_r;
     v.dinv = P->dinv;
     return v;
 }
@@ -567,7 +648,7 @@ template <typename PT>
 laker_status launch_utr(laker_ctx* ctx, int64_t n, const PrecView& pv, const double* r, PT* t, const PcgScalars* sc,
                         int gate) {
     if (pv.kind != PRECOND_CCCP) return LAKER_OK;
-    k_utr<PT><<<(unsigned)pv.n_r, 256, 0, ctx->stream>>>(n, pv, r, t, sc, gate);
+    k_utr<PT><<<(unsigned)((pv.n_r + 3) / 4), 256, 0, ctx->stream>>>(n, pv, r, t, sc, gate);
     LK_LAUNCHED(ctx);
     return LAKER_OK;
 }
@@ -583,7 +664,7 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
     ws.r = base; ws.z = base + n; ws.p[0] = base + 2 * n; ws.p[1] = base + 3 * n; ws.w = base + 4 * n;
     ws.w2 = base + 5 * n;
     // per-block partials of any of the kernels (the matrix-free finish runs one block per 128 rows)
-    const int64_t nb = std::max<int64_t>(4 * ctx->num_sms + 8, (n + 127) / 128 + 8);
+    const int64_t nb = std::max<int64_t>(8 * ctx->num_sms + 8, 4 * ((n + 127) / 128) + 8);
     if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
     const int nr = std::max(1, n_r);
     if ((st = lk_malloc(ctx, &ws.t, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
