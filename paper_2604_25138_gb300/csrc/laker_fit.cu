@@ -102,11 +102,13 @@ __global__ void k_reduce_splits(int64_t M, int64_t N, int nz, const T* __restric
 
 template <typename T>
 laker_status gemm(laker_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t Kd, const T* A, int64_t lda,
-                  const T* B, int64_t ldb, double lam, const double* X, int64_t ldx, double* out, int64_t ldo) {
+                  const T* B, int64_t ldb, double lam, const double* X, int64_t ldx, double* out, int64_t ldo,
+                  int64_t max_kchunk = 0) {
     const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
     int64_t want = std::max<int64_t>(1, (4 * ctx->num_sms + tiles - 1) / tiles);
     int64_t kchunk = (Kd + want - 1) / want;
     kchunk = std::max<int64_t>(64, (kchunk + 15) / 16 * 16);
+    if (max_kchunk > 0) kchunk = std::min(kchunk, max_kchunk);   // shorter float32 partial sums
     const int nz = (int)((Kd + kchunk - 1) / kchunk);
     T* parts = nullptr;
     laker_status st = lk_malloc(ctx, (void**)&parts, (size_t)nz * M * N * sizeof(T));
@@ -445,18 +447,26 @@ __global__ void k_jacobi_cols(double* __restrict__ S, double* __restrict__ V, in
     }
 }
 
-// off-diagonal and total squared Frobenius norms -> out[0], out[1] (single block)
-__global__ void k_offdiag(const double* __restrict__ S, int m, double* out) {
+// Squared Frobenius norms (single block): out[0] off-diagonal, out[1] total,
+// out[2] off-diagonal entries S_pq with max(S_pp, S_qq) >= tau (the couplings
+// that move P: inside the cluster below tau, phi(l) = (c + l)^-1/2 - c^-1/2 is
+// linear in l and needs no diagonalisation).
+__global__ void k_offdiag(const double* __restrict__ S, int m, double tau, double* out) {
     __shared__ double red[32];
-    double off = 0.0, tot = 0.0;
+    double off = 0.0, tot = 0.0, rel = 0.0;
     for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
         const double v = S[idx];
         tot = fma(v, v, tot);
-        if (idx / m != idx % m) off = fma(v, v, off);
+        const int64_t p = idx / m, q = idx % m;
+        if (p != q) {
+            off = fma(v, v, off);
+            if (fmax(S[p * m + p], S[q * m + q]) >= tau) rel = fma(v, v, rel);
+        }
     }
     off = lk::block_sum(off, red);
     tot = lk::block_sum(tot, red);
-    if (threadIdx.x == 0) { out[0] = off; out[1] = tot; }
+    rel = lk::block_sum(rel, red);
+    if (threadIdx.x == 0) { out[0] = off; out[1] = tot; out[2] = rel; }
 }
 
 __global__ void k_eye(double* V, int m) {
@@ -582,8 +592,16 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     if ((st = lk_malloc(ctx, (void**)&partials, (size_t)2 * NP * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&cn, sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&dst, sizeof(CccpState))) != LAKER_OK) return st;
+    // (float64 for every operator: with N_r near n the Gram is nearly singular
+    // and float32 errors of ~1e-7 break the definiteness of c D^-1 + M)
     if ((st = gemm<double>(ctx, true, false, nr, nr, n, U64, nr, U64, nr, 0.0, nullptr, 0, M, nr)) != LAKER_OK)
         return st;
+    float* U32 = nullptr;
+    if (op->precision != LAKER_FP64) {
+        if ((st = lk_malloc(ctx, (void**)&U32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
+        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, U64, U32);
+        LK_LAUNCHED(ctx);
+    }
     // ---- shrinkage-regularised CCCP
     if (rho < 0.0) rho = (nr >= n) ? 1e-3 : std::min(0.5, std::max(1e-3, gamma * (1.0 - (double)nr / n)));
     // direction features (inputs of the learned start, exported with P)
@@ -652,7 +670,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     if ((st = lk_malloc(ctx, (void**)&X, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&B0, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&B, (size_t)nr * nr * sizeof(double))) != LAKER_OK) return st;
-    if ((st = lk_malloc(ctx, (void**)&nrm, 2 * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&nrm, 3 * sizeof(double))) != LAKER_OK) return st;
     k_scaled_gram<<<gsz((int64_t)m * m), 256, 0, s>>>(m, nr, M, D, Sm);
     LK_LAUNCHED(ctx);
     k_eye<<<gsz((int64_t)m * m), 256, 0, s>>>(V, m);
@@ -665,27 +683,28 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         k_jacobi_rows<<<m / 2, 128, 0, s>>>(Sm, m, r, cs);
         k_jacobi_cols<<<m, 128, 0, s>>>(Sm, V, m, r, cs);
     }
-    k_offdiag<<<1, 1024, 0, s>>>(Sm, m, nrm);
+    const double tau = (op->precision == LAKER_FP64) ? 0.0 : 1e-2 * h.c;
+    k_offdiag<<<1, 1024, 0, s>>>(Sm, m, tau, nrm);
     LK_CUDA(ctx, cudaStreamEndCapture(s, &g));
     LK_CUDA(ctx, cudaGraphInstantiate(&ge, g, 0));
     // Stop once the off-diagonal Frobenius norm is below 1e-12 of the matrix
     // norm, or after 12 sweeps.  For float32 and split-bf16 operators, whose
-    // solves are judged by the true residual, also once it is at most 1e-2 c:
-    // the eigenpairs then diagonalise a matrix within |off| of S, and an
-    // eigenvalue moved by delta changes its factor in P = Sigma^-1/2 by at most
-    // delta / (2 c) relative, so P stays within 1 % of Sigma_*^-1/2 along every
-    // direction and positive definite.  The unrotated remainder couples the
-    // cluster of eigenvalues far below c, where (c + l)^-1/2 is flat.
-    double hn[2] = {0, 0};
+    // solves are judged by the true residual, also once the couplings that
+    // involve a diagonal entry >= c/100 weigh at most c/20: an unrotated
+    // coupling e changes P = Sigma^-1/2 by at most e / (2 c) relative, and
+    // inside the cluster below c/100 the factor phi(l) is linear in l up to
+    // (3/4)(l/c) relative, so P stays within a few % of Sigma_*^-1/2 along
+    // every direction and positive definite.
+    double hn[3] = {0, 0, 0};
     int sweeps = 0;
-    const double off_stop = (op->precision == LAKER_FP64) ? 0.0 : 1e-4 * h.c * h.c;
+    const double off_stop = (op->precision == LAKER_FP64) ? 0.0 : 2.5e-3 * h.c * h.c;
     for (int sweep = 0; sweep < 12; ++sweep) {
         LK_CUDA(ctx, cudaGraphLaunch(ge, s));
         ctx->launches += 2 * (m - 1) + 1;
         ++sweeps;
         LK_CUDA(ctx, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, s));
         LK_CUDA(ctx, cudaStreamSynchronize(s));
-        if (!(hn[0] > 1e-24 * hn[1]) || !(hn[0] > off_stop)) break;
+        if (!(hn[0] > 1e-24 * hn[1]) || !(hn[2] > off_stop)) break;
     }
     cudaGraphExecDestroy(ge);
     cudaGraphDestroy(g);
@@ -723,15 +742,12 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         double hl = 0.0;
         LK_CUDA(ctx, cudaMemcpyAsync(&hl, lmax, sizeof(double), cudaMemcpyDeviceToHost, s));
         LK_CUDA(ctx, cudaStreamSynchronize(s));
-        float *C32 = nullptr, *U32 = nullptr;
+        float* C32 = nullptr;
         double *phi = nullptr, *Ut = nullptr;
         if ((st = lk_malloc(ctx, (void**)&C32, (size_t)nr * nr * sizeof(float))) != LAKER_OK) return st;
         if ((st = lk_malloc(ctx, (void**)&phi, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
-        if ((st = lk_malloc(ctx, (void**)&U32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
         if ((st = lk_malloc(ctx, (void**)&Ut, (size_t)n * nr * sizeof(double))) != LAKER_OK) return st;
         k_utilde_coeffs<<<gsz((int64_t)nr * nr), 256, 0, s>>>(m, nr, Sm, V, D, h.c, hl, C32, phi);
-        LK_LAUNCHED(ctx);
-        k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, U64, U32);
         LK_LAUNCHED(ctx);
         if ((st = gemm<float>(ctx, false, false, n, nr, nr, U32, nr, C32, nr, 0.0, nullptr, 0, Ut, nr)) != LAKER_OK)
             return st;
@@ -744,6 +760,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         LK_LAUNCHED(ctx);
         LK_CUDA(ctx, cudaStreamSynchronize(s));
         for (void* ptr : {(void*)C32, (void*)U32, (void*)phi, (void*)Ut}) cudaFree(ptr);
+        U32 = nullptr;
     }
     LK_CUDA(ctx, cudaStreamSynchronize(s));
     for (void* ptr : {(void*)tmpv, (void*)M, (void*)A, (void*)D, (void*)Dn, (void*)q, (void*)partials, (void*)cn,
