@@ -395,55 +395,76 @@ __device__ __forceinline__ int rr_player(int pos, int round, int m) {
     return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1);
 }
 
-// One block per pair: compute the rotation from the 2x2 block and rotate rows p, q.
-__global__ void k_jacobi_rows(double* __restrict__ S, int m, int round, double* __restrict__ cs) {
-    const int k = blockIdx.x;
+// Rotations of one round of the round-robin pairing: pair k = (p, q), p < q,
+// gets (c, s) that zeroes its 2 x 2 block of S (t = sign(tau) /
+// (|tau| + sqrt(1 + tau^2)), tau = (S_qq - S_pp) / (2 S_pq)).
+__global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double* __restrict__ cs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m / 2) return;
     int p = rr_player(k, round, m), q = rr_player(m - 1 - k, round, m);
     if (p > q) { const int t = p; p = q; q = t; }
-    __shared__ double c_s[2];
-    if (threadIdx.x == 0) {
-        const double app = S[(int64_t)p * m + p], aqq = S[(int64_t)q * m + q], apq = S[(int64_t)p * m + q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0 && fabs(apq) > 1e-300) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-        }
-        c_s[0] = c;
-        c_s[1] = s;
-        cs[2 * k] = c;
-        cs[2 * k + 1] = s;
+    const double app = S[(int64_t)p * m + p], aqq = S[(int64_t)q * m + q], apq = S[(int64_t)p * m + q];
+    double c = 1.0, s = 0.0;
+    if (apq != 0.0 && fabs(apq) > 1e-300) {
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        c = 1.0 / sqrt(1.0 + t * t);
+        s = t * c;
     }
-    __syncthreads();
-    const double c = c_s[0], s = c_s[1];
-    if (s == 0.0) return;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const double a = S[(int64_t)p * m + j], b = S[(int64_t)q * m + j];
-        S[(int64_t)p * m + j] = c * a - s * b;
-        S[(int64_t)q * m + j] = s * a + c * b;
-    }
+    cs[2 * k] = c;
+    cs[2 * k + 1] = s;
 }
 
-// Rotate columns p, q of S and V for every pair; grid over rows.
-__global__ void k_jacobi_cols(double* __restrict__ S, double* __restrict__ V, int m, int round,
-                              const double* __restrict__ cs) {
-    const int i = blockIdx.x;
-    for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
-        int p = rr_player(k, round, m), q = rr_player(m - 1 - k, round, m);
-        if (p > q) { const int t = p; p = q; q = t; }
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        if (s == 0.0) continue;
-        double* Si = S + (int64_t)i * m;
-        const double a = Si[p], b = Si[q];
-        Si[p] = c * a - s * b;
-        Si[q] = s * a + c * b;
-        if (i == p) Si[q] = 0.0;
-        if (i == q) Si[p] = 0.0;
-        double* Vi = V + (int64_t)i * m;
-        const double va = Vi[p], vb = Vi[q];
-        Vi[p] = c * va - s * vb;
-        Vi[q] = s * va + c * vb;
+// One round of the two-sided update in a single pass over S and V, from the
+// input buffers into the output buffers.  Thread (i, j) with j >= i (pairs of
+// the round) forms the 2 x 2 block R_i^T S_ij R_j of rows (p_i, q_i) and
+// columns (p_j, q_j) and writes it and its transpose (S stays symmetric; the
+// diagonal blocks become diagonal); threads of the second range rotate the
+// columns (p_j, q_j) of one row of V.  Consecutive threads take consecutive j.
+__global__ void __launch_bounds__(256)
+k_jac_update(const double* __restrict__ Sin, double* __restrict__ Sout, const double* __restrict__ Vin,
+             double* __restrict__ Vout, int m, int round, const double* __restrict__ cs) {
+    const int half = m / 2;
+    const int64_t ns = (int64_t)half * half, total = ns + (int64_t)m * half;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < ns) {
+            const int i = (int)(e / half), j = (int)(e % half);
+            if (j < i) continue;
+            int pi = rr_player(i, round, m), qi = rr_player(m - 1 - i, round, m);
+            if (pi > qi) { const int t = pi; pi = qi; qi = t; }
+            int pj = rr_player(j, round, m), qj = rr_player(m - 1 - j, round, m);
+            if (pj > qj) { const int t = pj; pj = qj; qj = t; }
+            const double ci = cs[2 * i], si = cs[2 * i + 1], cj = cs[2 * j], sj = cs[2 * j + 1];
+            const double a = Sin[(int64_t)pi * m + pj], b = Sin[(int64_t)pi * m + qj];
+            const double c = Sin[(int64_t)qi * m + pj], d = Sin[(int64_t)qi * m + qj];
+            const double r0a = ci * a - si * c, r0b = ci * b - si * d;
+            const double r1a = si * a + ci * c, r1b = si * b + ci * d;
+            double o00 = cj * r0a - sj * r0b, o01 = sj * r0a + cj * r0b;
+            double o10 = cj * r1a - sj * r1b, o11 = sj * r1a + cj * r1b;
+            if (i == j) {
+                o01 = 0.0;
+                o10 = 0.0;
+            }
+            Sout[(int64_t)pi * m + pj] = o00;
+            Sout[(int64_t)pi * m + qj] = o01;
+            Sout[(int64_t)qi * m + pj] = o10;
+            Sout[(int64_t)qi * m + qj] = o11;
+            if (i != j) {
+                Sout[(int64_t)pj * m + pi] = o00;
+                Sout[(int64_t)qj * m + pi] = o01;
+                Sout[(int64_t)pj * m + qi] = o10;
+                Sout[(int64_t)qj * m + qi] = o11;
+            }
+        } else {
+            const int64_t f = e - ns;
+            const int row = (int)(f / half), j = (int)(f % half);
+            int pj = rr_player(j, round, m), qj = rr_player(m - 1 - j, round, m);
+            if (pj > qj) { const int t = pj; pj = qj; qj = t; }
+            const double cj = cs[2 * j], sj = cs[2 * j + 1];
+            const double va = Vin[(int64_t)row * m + pj], vb = Vin[(int64_t)row * m + qj];
+            Vout[(int64_t)row * m + pj] = cj * va - sj * vb;
+            Vout[(int64_t)row * m + qj] = sj * va + cj * vb;
+        }
     }
 }
 
@@ -675,18 +696,30 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     LK_LAUNCHED(ctx);
     k_eye<<<gsz((int64_t)m * m), 256, 0, s>>>(V, m);
     LK_LAUNCHED(ctx);
-    // one sweep = m-1 rounds, captured once into a graph
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    LK_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int r = 0; r < m - 1; ++r) {
-        k_jacobi_rows<<<m / 2, 128, 0, s>>>(Sm, m, r, cs);
-        k_jacobi_cols<<<m, 128, 0, s>>>(Sm, V, m, r, cs);
-    }
+    // One sweep = m - 1 rounds, each a rotation kernel and one fused update pass
+    // from one buffer pair into the other.  m - 1 is odd, so sweeps alternate
+    // between starting from (Sm, V) and from (S2, V2): two graphs.
+    double *S2 = nullptr, *V2 = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&S2, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&V2, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     const double tau = (op->precision == LAKER_FP64) ? 0.0 : 1e-2 * h.c;
-    k_offdiag<<<1, 1024, 0, s>>>(Sm, m, tau, nrm);
-    LK_CUDA(ctx, cudaStreamEndCapture(s, &g));
-    LK_CUDA(ctx, cudaGraphInstantiate(&ge, g, 0));
+    const int64_t upd_work = (int64_t)(m / 2) * (m / 2) + (int64_t)m * (m / 2);
+    const unsigned upd_blocks = (unsigned)std::min<int64_t>((upd_work + 255) / 256, 8 * ctx->num_sms);
+    cudaGraph_t gr[2] = {nullptr, nullptr};
+    cudaGraphExec_t ge[2] = {nullptr, nullptr};
+    for (int start = 0; start < 2; ++start) {
+        LK_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        double *Sa = start ? S2 : Sm, *Sb = start ? Sm : S2, *Va = start ? V2 : V, *Vb = start ? V : V2;
+        for (int r = 0; r < m - 1; ++r) {
+            k_jac_rot<<<(unsigned)((m / 2 + 127) / 128), 128, 0, s>>>(Sa, m, r, cs);
+            k_jac_update<<<upd_blocks, 256, 0, s>>>(Sa, Sb, Va, Vb, m, r, cs);
+            std::swap(Sa, Sb);
+            std::swap(Va, Vb);
+        }
+        k_offdiag<<<1, 1024, 0, s>>>(Sa, m, tau, nrm);
+        LK_CUDA(ctx, cudaStreamEndCapture(s, &gr[start]));
+        LK_CUDA(ctx, cudaGraphInstantiate(&ge[start], gr[start], 0));
+    }
     // Stop once the off-diagonal Frobenius norm is below 1e-12 of the matrix
     // norm, or after 12 sweeps.  For float32 and split-bf16 operators, whose
     // solves are judged by the true residual, also once the couplings that
@@ -698,16 +731,27 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     double hn[3] = {0, 0, 0};
     int sweeps = 0;
     const double off_stop = (op->precision == LAKER_FP64) ? 0.0 : 2.5e-3 * h.c * h.c;
+    int cur = 0;   // 0: the latest S, V are in (Sm, V); 1: in (S2, V2)
     for (int sweep = 0; sweep < 12; ++sweep) {
-        LK_CUDA(ctx, cudaGraphLaunch(ge, s));
+        LK_CUDA(ctx, cudaGraphLaunch(ge[cur], s));
+        cur ^= 1;
         ctx->launches += 2 * (m - 1) + 1;
         ++sweeps;
         LK_CUDA(ctx, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, s));
         LK_CUDA(ctx, cudaStreamSynchronize(s));
         if (!(hn[0] > 1e-24 * hn[1]) || !(hn[2] > off_stop)) break;
     }
-    cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
+    for (int k = 0; k < 2; ++k) {
+        cudaGraphExecDestroy(ge[k]);
+        cudaGraphDestroy(gr[k]);
+    }
+    if (cur == 1) {   // bring the result back to (Sm, V)
+        LK_CUDA(ctx, cudaMemcpyAsync(Sm, S2, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        LK_CUDA(ctx, cudaMemcpyAsync(V, V2, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    LK_CUDA(ctx, cudaStreamSynchronize(s));
+    cudaFree(S2);
+    cudaFree(V2);
     P->kind = PRECOND_CCCP;
     P->n = n;
     P->n_r = nr;
