@@ -69,6 +69,7 @@ typedef struct {
     double rho;          /* shrinkage used */
     double change;       /* last relative Frobenius change |S_{t+1}-S_t|_F/|S_t|_F */
     int status;          /* laker_status of the fit */
+    int eig_sweeps;      /* Jacobi sweeps of the eigendecomposition behind Sigma_*^-1/2 */
 } laker_fit_info;
 
 typedef struct {
@@ -271,16 +272,39 @@ laker_status laker_fit_preconditioner_learned(laker_ctx* ctx, const laker_op* op
 /*
  * Radio-map reconstruction (Sec. III-A, Eq. sc-radio-map-reconstruction;
  * Algorithm 1, reconstruction stage):  out_m = sum_i exp(scale <qg_m, q_i>) alpha_i.
- *   Qg   m x d query embeddings (device float64);  alpha, out device float64.
- * Computed in the operator's precision (FP64, or split-bf16 logits with
- * float32 exp and float64 partial sums).
+ *   Qg   m x d query embeddings (device float64, row-major);  alpha (n), out (m)
+ *   device float64.  Synchronous on the context's stream; allocates scratch.
+ * laker_eval_map is laker_eval_map_method with LAKER_MAP_AUTO.
+ * Methods:
+ *   LAKER_MAP_DOUBLE_FLOAT  float64 kernel for FP64 operators; for FP32 and
+ *       BF16X3 operators double-float arithmetic on the float32 pipes (every
+ *       kernel value to ~1e-14 relative); d <= 64.
+ *   LAKER_MAP_TENSOR  exp(L) = 1 + L + L^2/2 + L^3 g(L) with L = scale <qg, q>:
+ *       the first three terms from float64 alpha-weighted moments of the
+ *       training embeddings, the remainder from tcgen05 logits of a three-piece
+ *       bf16 split and a float32 polynomial for g (map error ~1e-5 relative to
+ *       |y| on the benchmark instances, ~1e-4 dB).  Applies when
+ *       scale * max|qg_m| * max|q_i| <= 1/2 and d <= 64; otherwise
+ *       LAKER_ERR_UNSUPPORTED.
+ *   LAKER_MAP_AUTO  FP64 operators: the float64 kernel; FP32 and BF16X3
+ *       operators: LAKER_MAP_TENSOR where it applies, else LAKER_MAP_DOUBLE_FLOAT.
+ * Errors: LAKER_ERR_ARG for m < 1, null pointers or an unknown method;
+ *         LAKER_ERR_TIMEOUT if a bounded wait of the tensor-core kernel expired.
  */
+typedef enum {
+    LAKER_MAP_AUTO = 0,
+    LAKER_MAP_DOUBLE_FLOAT = 1,
+    LAKER_MAP_TENSOR = 2
+} laker_map_method;
 laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
                             const double* alpha, double* out);
+laker_status laker_eval_map_method(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                                   const double* alpha, double* out, int method);
 
 /*
  * Radio map without device allocation (no counterpart in the paper; a
- * deployment variant of laker_eval_map with the same arguments and results).
+ * deployment variant of laker_eval_map_method with LAKER_MAP_DOUBLE_FLOAT, same
+ * arguments and results).
  * For callers that cannot call cudaMalloc -- services whose device memory is
  * owned and pre-reserved by another allocator, or loops that must not
  * synchronise the device, as cudaMalloc and cudaFree do.  Scratch comes from a

@@ -330,13 +330,19 @@ laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batc
     return pcg_solve_batched(ctx, count, items, tol, max_iter, refine_every, infos, done_ms);
 }
 
-laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
-                            double* out) {
+laker_status laker_eval_map_method(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                                   const double* alpha, double* out, int method) {
     laker_status st = check_ctx(ctx);
     if (st != LAKER_OK) return st;
     if (!op || !Qg || !alpha || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
     if (m < 1) return set_error(ctx, LAKER_ERR_ARG, "need m >= 1");
-    return eval_map(ctx, op, Qg, m, alpha, out);
+    if (method < LAKER_MAP_AUTO || method > LAKER_MAP_TENSOR) return set_error(ctx, LAKER_ERR_ARG, "unknown map method");
+    return eval_map(ctx, op, Qg, m, alpha, out, method);
+}
+
+laker_status laker_eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
+                            double* out) {
+    return laker_eval_map_method(ctx, op, Qg, m, alpha, out, LAKER_MAP_AUTO);
 }
 
 }  // extern "C"

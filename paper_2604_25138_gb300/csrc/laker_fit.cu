@@ -28,12 +28,15 @@ constexpr int NB = 32;   // panel / tile edge of the small dense kernels
 // ---------------------------------------------------------------------------
 // Generic SIMT GEMM with split-K:  C_z = op(A) op(B) over k in split z.
 // op(A)(i,k) = TA ? A[k*lda+i] : A[i*lda+k];  op(B)(k,j) = TB ? B[j*ldb+k] : B[k*ldb+j]
+// sym: the product is symmetric (a Gram matrix); only tiles on or above the
+// diagonal are computed and the reduction mirrors the rest.
 // ---------------------------------------------------------------------------
 template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(256)
 k_gemm(int64_t M, int64_t N, int64_t Kd, const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
-       int64_t ldb, T* __restrict__ C, int64_t ldc, int64_t kchunk) {
+       int64_t ldb, T* __restrict__ C, int64_t ldc, int64_t kchunk, int sym) {
     constexpr int BM = 64, BN = 64, BK = 16;
+    if (sym && blockIdx.y > blockIdx.x) return;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -90,12 +93,14 @@ k_gemm(int64_t M, int64_t N, int64_t Kd, const T* __restrict__ A, int64_t lda, c
 template <typename T>
 __global__ void k_reduce_splits(int64_t M, int64_t N, int nz, const T* __restrict__ parts, int64_t ldp,
                                 double lam, const double* __restrict__ X, int64_t ldx, double* __restrict__ out,
-                                int64_t ldo) {
+                                int64_t ldo, int sym) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
     const int64_t i = idx / N, j = idx % N;
+    const bool mirror = sym && (i / 64 > j / 64);
+    const int64_t src = mirror ? j * ldp + i : i * ldp + j;
     double s = 0.0;
-    for (int z = 0; z < nz; ++z) s += (double)parts[(int64_t)z * M * ldp + i * ldp + j];
+    for (int z = 0; z < nz; ++z) s += (double)parts[(int64_t)z * M * ldp + src];
     if (X) s = fma(lam, X[i * ldx + j], s);
     out[i * ldo + j] = s;
 }
@@ -103,8 +108,10 @@ __global__ void k_reduce_splits(int64_t M, int64_t N, int nz, const T* __restric
 template <typename T>
 laker_status gemm(laker_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t Kd, const T* A, int64_t lda,
                   const T* B, int64_t ldb, double lam, const double* X, int64_t ldx, double* out, int64_t ldo,
-                  int64_t max_kchunk = 0) {
-    const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+                  int64_t max_kchunk = 0, bool sym = false) {
+    if (sym && (M != N || X)) return set_error(ctx, LAKER_ERR_ARG, "symmetric gemm: square, no addend");
+    const int64_t nt = (M + 63) / 64;
+    const int64_t tiles = sym ? nt * (nt + 1) / 2 : nt * ((N + 63) / 64);
     int64_t want = std::max<int64_t>(1, (4 * ctx->num_sms + tiles - 1) / tiles);
     int64_t kchunk = (Kd + want - 1) / want;
     kchunk = std::max<int64_t>(64, (kchunk + 15) / 16 * 16);
@@ -114,13 +121,13 @@ laker_status gemm(laker_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_
     laker_status st = lk_malloc(ctx, (void**)&parts, (size_t)nz * M * N * sizeof(T));
     if (st != LAKER_OK) return st;
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)nz);
-    if (!ta && !tb) k_gemm<T, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
-    else if (ta && !tb) k_gemm<T, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
-    else if (!ta && tb) k_gemm<T, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
-    else k_gemm<T, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk);
+    if (!ta && !tb) k_gemm<T, false, false><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk, sym);
+    else if (ta && !tb) k_gemm<T, true, false><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk, sym);
+    else if (!ta && tb) k_gemm<T, false, true><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk, sym);
+    else k_gemm<T, true, true><<<grid, 256, 0, ctx->stream>>>(M, N, Kd, A, lda, B, ldb, parts, N, kchunk, sym);
     LK_LAUNCHED(ctx);
     k_reduce_splits<T><<<(unsigned)((M * N + 255) / 256), 256, 0, ctx->stream>>>(M, N, nz, parts, N, lam, X, ldx,
-                                                                                  out, ldo);
+                                                                                  out, ldo, sym ? 1 : 0);
     LK_LAUNCHED(ctx);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(parts);
@@ -210,89 +217,146 @@ __global__ void k_cccp_form(int NP, int nr, const double* __restrict__ M, const 
     A[idx] = v;
 }
 
-// Cholesky of the diagonal tile jb (one block of NB x NB threads).
-__global__ void __launch_bounds__(NB * NB) k_potrf_diag(double* __restrict__ A, int lda, int jb, int* status) {
-    __shared__ double T[NB][NB + 1];
-    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
-    const int64_t g0 = (int64_t)jb * NB;
-    T[r][c] = A[(g0 + r) * lda + g0 + c];
-    __syncthreads();
-    for (int j = 0; j < NB; ++j) {
-        if (r == j && c == j) {
-            const double d = T[j][j];
-            if (!(d > 0.0) || !isfinite(d)) { *status = LAKER_ERR_NOT_SPD; T[j][j] = 1.0; }
-            else T[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        if (c == j && r > j) T[r][j] /= T[j][j];
-        __syncthreads();
-        if (r > j && c > j && c <= r) T[r][c] = fma(-T[r][j], T[c][j], T[r][c]);
-        __syncthreads();
-    }
-    A[(g0 + r) * lda + g0 + c] = (c <= r) ? T[r][c] : 0.0;
+// 1/sqrt(p) for p > 0: a float32 estimate refined by two Newton steps
+// y <- y (3 - p y^2) / 2 (relative error ~1e-7 -> ~1e-14 -> float64 rounding).
+// Float64 division and square root are long dependent sequences on this GPU,
+// and a pivot sits on the critical path of every column of the factorisation.
+__device__ __forceinline__ double rsqrt_newton(double p) {
+    double y = (p > 1e-30 && p < 1e30) ? (double)rsqrtf((float)p) : 1.0 / sqrt(p);
+    const double h = 0.5 * p;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
 }
 
-// Row blocks ib in (jb, nrb): A_ib,jb <- A_ib,jb L_jb^-T (one block per row block, warp per row).
-__global__ void __launch_bounds__(NB * NB) k_trsm_panel(double* __restrict__ A, int lda, int jb) {
-    __shared__ double L[NB][NB + 1];
-    const int ib = jb + 1 + blockIdx.x;
-    const int lane = threadIdx.x % NB, row = threadIdx.x / NB;
+// Cholesky of the diagonal tile jb (one block of NB x NB threads, warp c =
+// column c, lane = row) and dinv[j] = 1 / L_jj for the panel solve.  One
+// barrier per column j: warp j writes L's column j = T_.j y_j into the output
+// tile, the columns right of j take the rank-1 update from the unscaled column
+// j, T_rc -= T_rj T_cj y_j^2, and the thread that updates the next pivot
+// T_j+1,j+1 forms y_j+1 = 1/sqrt(pivot) at once.  A float64 instruction costs
+// a warp's full issue whatever its active lanes, so each step keeps the active
+// threads to as few warps as it can.
+__global__ void __launch_bounds__(NB * NB) k_potrf_diag(double* __restrict__ A, int lda, int jb, int* status,
+                                                       double* __restrict__ dinv) {
+    __shared__ double T[NB][NB + 1];
+    __shared__ double Lo[NB][NB + 1];
+    __shared__ double yv[2][2];
     const int64_t g0 = (int64_t)jb * NB;
-    L[row][lane] = A[(g0 + row) * lda + g0 + lane];
+    const int rr = threadIdx.x / NB, cc = threadIdx.x % NB;   // coalesced copy in and out
+    T[rr][cc] = A[(g0 + rr) * lda + g0 + cc];
+    Lo[rr][cc] = 0.0;
+    const int c = threadIdx.x / NB, r = threadIdx.x % NB;
+    auto pivot = [&](int j) {
+        double p = T[j][j];
+        if (!(p > 0.0) || !isfinite(p)) { *status = LAKER_ERR_NOT_SPD; p = 1.0; }
+        const double y = rsqrt_newton(p);
+        yv[j & 1][0] = y;
+        yv[j & 1][1] = y * y;
+        dinv[j] = y;
+        Lo[j][j] = p * y;
+    };
     __syncthreads();
-    const int64_t gr = (int64_t)ib * NB + row;
-    const double a = A[gr * lda + g0 + lane];
+    if (threadIdx.x == 0) pivot(0);
+    __syncthreads();
+    for (int j = 0; j < NB; ++j) {
+        if (c == j && r > j) Lo[r][j] = T[r][j] * yv[j & 1][0];
+        if (c > j && r >= c) {
+            T[r][c] = fma(-T[r][j] * yv[j & 1][1], T[c][j], T[r][c]);
+            if (r == j + 1 && c == j + 1) pivot(j + 1);
+        }
+        __syncthreads();
+    }
+    A[(g0 + rr) * lda + g0 + cc] = Lo[rr][cc];
+}
+
+// Rows r in [(jb + 1) NB, rows_end) of the panel columns:  A_r,jb <- A_r,jb L_jb^-T
+// by forward substitution along each row (warp per row, TR_ROWS rows per block),
+// with L and the row's right-hand side pre-scaled by dinv so that a step is one
+// subtraction and one FMA.
+constexpr int TR_ROWS = 16;
+__global__ void __launch_bounds__(TR_ROWS * NB) k_trsm_panel(double* __restrict__ A, int lda, int jb, int rows_end,
+                                                             const double* __restrict__ dinv) {
+    __shared__ double L[NB][NB + 1];   // L_jk / L_jj
+    const int lane = threadIdx.x % NB, w = threadIdx.x / NB;
+    const int64_t g0 = (int64_t)jb * NB;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+        const int i = idx / NB, k = idx % NB;
+        L[i][k] = A[(g0 + i) * lda + g0 + k] * dinv[i];
+    }
+    __syncthreads();
+    const int64_t gr = (int64_t)(jb + 1) * NB + (int64_t)blockIdx.x * TR_ROWS + w;
+    if (gr >= rows_end) return;
+    const double a = A[gr * lda + g0 + lane] * dinv[lane];
     double acc = 0.0, x = 0.0;
     for (int j = 0; j < NB; ++j) {
         double xj = 0.0;
-        if (lane == j) { x = (a - acc) / L[j][j]; xj = x; }
+        if (lane == j) { x = a - acc; xj = x; }
         xj = __shfl_sync(0xffffffffu, xj, j);
         if (lane > j) acc = fma(L[lane][j], xj, acc);
     }
     A[gr * lda + g0 + lane] = x;
 }
 
-// Trailing update after panel jb: A_ib,kb -= A_ib,jb A_kb,jb^T over
-// top tiles (jb < kb <= ib < ncb) and bottom tiles (ncb <= ib < 2 ncb, jb < kb < ncb).
-__global__ void __launch_bounds__(256) k_syrk_update(double* __restrict__ A, int lda, int jb, int ncb) {
-    const int m = ncb - jb - 1;
-    const int top = m * (m + 1) / 2;
-    int t = blockIdx.x, ib, kb;
+// Trailing update after panel jb: A_ij -= sum_k A_ik A_jk over the panel's NB
+// columns k, for the lower triangle of the top (r0 <= j <= i < NP) and the whole
+// bottom (NP <= i < 2 NP, r0 <= j < NP), r0 = (jb + 1) NB.  64 x 64 output tiles
+// anchored at r0 (ragged at the ends), 4 x 4 per thread.
+constexpr int UT = 64;
+__global__ void __launch_bounds__(256) k_syrk_update(double* __restrict__ A, int lda, int jb, int NP) {
+    const int r0 = (jb + 1) * NB;
+    const int mt = (NP - r0 + UT - 1) / UT;
+    const int top = mt * (mt + 1) / 2;
+    int t = blockIdx.x, row0, rend;
+    int col0;
+    bool diag = false;
     if (t < top) {
-        int rI = 0;
-        while (t >= rI + 1) { t -= rI + 1; ++rI; }
-        ib = jb + 1 + rI;
-        kb = jb + 1 + t;
+        int ti = 0;
+        while (t >= ti + 1) { t -= ti + 1; ++ti; }
+        row0 = r0 + ti * UT;
+        col0 = r0 + t * UT;
+        rend = NP;
+        diag = (t == ti);
     } else {
         t -= top;
-        ib = ncb + t / m;
-        kb = jb + 1 + t % m;
+        row0 = NP + (t / mt) * UT;
+        col0 = r0 + (t % mt) * UT;
+        rend = 2 * NP;
     }
-    __shared__ double X[NB][NB + 1], Y[NB][NB + 1];
+    __shared__ double Xs[NB][UT + 1], Ys[NB][UT + 1];
     const int64_t cj = (int64_t)jb * NB;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) {
-        const int r = idx / NB, c = idx % NB;
-        X[r][c] = A[((int64_t)ib * NB + r) * lda + cj + c];
-        Y[r][c] = A[((int64_t)kb * NB + r) * lda + cj + c];
+    for (int idx = threadIdx.x; idx < UT * NB; idx += 256) {
+        const int r = idx / NB, k = idx % NB;
+        const int gr = row0 + r, gc = col0 + r;
+        Xs[k][r] = (gr < rend) ? A[(int64_t)gr * lda + cj + k] : 0.0;
+        Ys[k][r] = (gc < NP) ? A[(int64_t)gc * lda + cj + k] : 0.0;
     }
     __syncthreads();
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+#pragma unroll 4
     for (int k = 0; k < NB; ++k) {
-        const double x0 = X[ty][k], x1 = X[ty + 16][k];
-        const double y0 = Y[tx][k], y1 = Y[tx + 16][k];
-        acc[0][0] = fma(x0, y0, acc[0][0]);
-        acc[0][1] = fma(x0, y1, acc[0][1]);
-        acc[1][0] = fma(x1, y0, acc[1][0]);
-        acc[1][1] = fma(x1, y1, acc[1][1]);
+        double x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { x[u] = Xs[k][ty + 16 * u]; y[u] = Ys[k][tx + 16 * u]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < 4; ++u) {
+        const int gr = row0 + ty + 16 * u;
 #pragma unroll
-        for (int v = 0; v < 2; ++v) {
-            const int64_t gi = (int64_t)ib * NB + ty + 16 * u, gk = (int64_t)kb * NB + tx + 16 * v;
-            A[gi * lda + gk] -= acc[u][v];
+        for (int v = 0; v < 4; ++v) {
+            const int gc = col0 + tx + 16 * v;
+            if (gr < rend && gc < NP && (!diag || gc <= gr)) A[(int64_t)gr * lda + gc] -= acc[u][v];
         }
+    }
 }
 
 // q_k = (M_kk - |row k of the bottom factor|^2) / c   (warp per k)
@@ -612,10 +676,13 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     if ((st = lk_malloc(ctx, (void**)&q, (size_t)NP * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&partials, (size_t)2 * NP * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&cn, sizeof(double))) != LAKER_OK) return st;
+    double* dinv = nullptr;   // 1 / L_jj of the current diagonal tile
+    if ((st = lk_malloc(ctx, (void**)&dinv, NB * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&dst, sizeof(CccpState))) != LAKER_OK) return st;
     // (float64 for every operator: with N_r near n the Gram is nearly singular
     // and float32 errors of ~1e-7 break the definiteness of c D^-1 + M)
-    if ((st = gemm<double>(ctx, true, false, nr, nr, n, U64, nr, U64, nr, 0.0, nullptr, 0, M, nr)) != LAKER_OK)
+    if ((st = gemm<double>(ctx, true, false, nr, nr, n, U64, nr, U64, nr, 0.0, nullptr, 0, M, nr, 0, true)) !=
+        LAKER_OK)
         return st;
     float* U32 = nullptr;
     if (op->precision != LAKER_FP64) {
@@ -660,15 +727,15 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         k_cccp_form<<<gsz((int64_t)2 * NP * NP), 256, 0, s>>>(NP, nr, M, D, dst, A);
         LK_LAUNCHED(ctx);
         for (int jb = 0; jb < ncb; ++jb) {
-            k_potrf_diag<<<1, NB * NB, 0, s>>>(A, NP, jb, dstatus);
+            k_potrf_diag<<<1, NB * NB, 0, s>>>(A, NP, jb, dstatus, dinv);
             LK_LAUNCHED(ctx);
-            const int below = 2 * ncb - jb - 1;
-            k_trsm_panel<<<below, NB * NB, 0, s>>>(A, NP, jb);
+            const int below = 2 * NP - (jb + 1) * NB;
+            k_trsm_panel<<<(below + TR_ROWS - 1) / TR_ROWS, TR_ROWS * NB, 0, s>>>(A, NP, jb, 2 * NP, dinv);
             LK_LAUNCHED(ctx);
-            const int m = ncb - jb - 1;
-            const int tiles = m * (m + 1) / 2 + ncb * m;
-            if (tiles > 0) {
-                k_syrk_update<<<tiles, 256, 0, s>>>(A, NP, jb, ncb);
+            const int mt = (NP - (jb + 1) * NB + UT - 1) / UT;
+            const int tiles = mt * (mt + 1) / 2 + ((NP + UT - 1) / UT) * mt;
+            if (mt > 0) {
+                k_syrk_update<<<tiles, 256, 0, s>>>(A, NP, jb, NP);
                 LK_LAUNCHED(ctx);
             }
         }
@@ -808,7 +875,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     }
     LK_CUDA(ctx, cudaStreamSynchronize(s));
     for (void* ptr : {(void*)tmpv, (void*)M, (void*)A, (void*)D, (void*)Dn, (void*)q, (void*)partials, (void*)cn,
-                      (void*)dst, (void*)Sm, (void*)V, (void*)cs, (void*)X, (void*)B0, (void*)B, (void*)nrm})
+                      (void*)dst, (void*)Sm, (void*)V, (void*)cs, (void*)X, (void*)B0, (void*)B, (void*)nrm, (void*)dinv})
         cudaFree(ptr);
     if (info) {
         info->iterations = h.iter;
@@ -817,6 +884,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
         info->rho = rho;
         info->change = h.change;
         info->status = h.status;
+        info->eig_sweeps = sweeps;
     }
     if (h.status != 0) return set_error(ctx, (laker_status)h.status, "CCCP factorisation failed");
     return LAKER_OK;

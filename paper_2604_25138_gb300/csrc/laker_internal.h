@@ -122,7 +122,10 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
                       laker_setnet* net = nullptr, const float* X = nullptr, int mode = 0);
 // laker_map.cu
 laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
-                      const double* alpha, double* out);
+                      const double* alpha, double* out, int method);
+// laker_map_tc.cu (tensor-core map; *applied = false when its logit bound fails)
+laker_status eval_map_tc(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
+                         const double* alpha, double* out, bool* applied);
 // laker_mf.cu (matrix-free operator)
 laker_status mf_prepare(laker_ctx* ctx, laker_op* op);
 void mf_release(laker_op* op);

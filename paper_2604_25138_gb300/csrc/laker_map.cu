@@ -192,7 +192,14 @@ static laker_status eval_map_df(laker_ctx* ctx, const laker_op* op, const double
 }
 
 laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
-                      double* out) {
+                      double* out, int method) {
+    if (method == LAKER_MAP_TENSOR || (method == LAKER_MAP_AUTO && op->precision != LAKER_FP64)) {
+        bool applied = false;
+        const laker_status st = eval_map_tc(ctx, op, Qg, m, alpha, out, &applied);
+        if (st != LAKER_OK || applied) return st;
+        if (method == LAKER_MAP_TENSOR)
+            return set_error(ctx, LAKER_ERR_UNSUPPORTED, "tensor-core map: d > 64 or scale max|qg| max|q| > 1/2");
+    }
     if (op->precision != LAKER_FP64) return eval_map_df(ctx, op, Qg, m, alpha, out);
     const int64_t n = op->n;
     const int64_t mt = (m + BT - 1) / BT, nt = (n + BT - 1) / BT;
@@ -219,7 +226,8 @@ laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int6
 // and fully pre-reserved by another allocator (a framework's caching
 // allocator, a fixed-budget real-time process), or loops that must not
 // synchronise the device, which cudaMalloc and cudaFree do.  This variant
-// launches the same map kernels as laker_eval_map but takes its scratch (the
+// launches the same map kernels as the double-float / float64 method of
+// laker_eval_map_method but takes its scratch (the
 // double-float copies of the inputs and the per-slice partial sums) from the
 // static device array below instead of allocating it.
 //

@@ -33,7 +33,8 @@ class LakerError(RuntimeError):
 
 class FitInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("c", ctypes.c_double),
-                ("rho", ctypes.c_double), ("change", ctypes.c_double), ("status", ctypes.c_int)]
+                ("rho", ctypes.c_double), ("change", ctypes.c_double), ("status", ctypes.c_int),
+                ("eig_sweeps", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -93,6 +94,7 @@ def library() -> ctypes.CDLL:
         "laker_precond_export": (i32, [vp, vp, vp, vp, vp]),
         "laker_pcg_solve": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
         "laker_eval_map": (i32, [vp, vp, vp, i64, vp, vp]),
+        "laker_eval_map_method": (i32, [vp, vp, vp, i64, vp, vp, i32]),
         "laker_eval_map_noalloc": (i32, [vp, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -432,14 +434,17 @@ def laker_pcg_solve_batched(ctx: Context, items, tol: float, max_iter: int = 100
             [done[k] for k in range(count)])
 
 
+MAP_AUTO, MAP_DOUBLE_FLOAT, MAP_TENSOR = 0, 1, 2
+
+
 def laker_eval_map(ctx: Context, op: Operator, Qg: torch.Tensor, alpha: torch.Tensor,
-                   out: torch.Tensor | None = None) -> torch.Tensor:
+                   out: torch.Tensor | None = None, method: int = MAP_AUTO) -> torch.Tensor:
     m = Qg.shape[0]
     if out is None:
         out = torch.empty(m, dtype=torch.float64, device=alpha.device)
     with ctx:
-        ctx.check(library().laker_eval_map(ctx.handle, op.handle, _ptr(Qg, "Qg", m * op.d), m,
-                                           _ptr(alpha, "alpha", op.n), _ptr(out, "out", m)))
+        ctx.check(library().laker_eval_map_method(ctx.handle, op.handle, _ptr(Qg, "Qg", m * op.d), m,
+                                                  _ptr(alpha, "alpha", op.n), _ptr(out, "out", m), int(method)))
     return out
 
 

@@ -2,10 +2,13 @@
 profiling one kernel at a time with Nsight Compute.
 
     python -m paper_2604_25138_gb300.profile_cases operator --n 16384 --precision bf16x3 --reps 5
+    python -m paper_2604_25138_gb300.profile_cases fit --n 16384
     python -m paper_2604_25138_gb300.profile_cases solve --n 16384
 
 `operator` builds the operator of the benchmark instance (clustered layout,
-d = 32, lambda = 1e-4) and applies it `reps` times; `solve` also fits the CCCP
+d = 32, lambda = 1e-4) and applies it `reps` times; `fit` builds it and fits
+the CCCP preconditioner only (printing how many kernels ran before the fit, for
+a launch window over the fit); `solve` also fits the CCCP
 preconditioner (N_r from the default schedule) and runs the mixed PCG solve;
 `map` evaluates the radio map on a grid of m points.  All inputs are the seeded
 synthetic ones of `synth.py`; nothing here is timed for reporting.
@@ -23,7 +26,7 @@ PRECISIONS = {"fp64": L.FP64, "fp32": L.FP32, "bf16x3": L.BF16X3}
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["operator", "solve", "map"])
+    ap.add_argument("case", choices=["operator", "fit", "solve", "map"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--d", type=int, default=32)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16x3")
@@ -45,8 +48,13 @@ def main(argv=None):
         print(f"operator n={a.n} d={a.d} {a.precision}: {a.reps} products, |w| = {float(w.norm()):.6e}")
         return
     Z = dev(synth.directions(a.n, synth.default_num_directions(a.n), a.seed))
+    torch.cuda.synchronize()
+    print(f"launches before fit {ctx.launches()}", flush=True)
     P = L.laker_fit_preconditioner(ctx, op, Z)
     torch.cuda.synchronize()
+    if a.case == "fit":
+        print(f"fit n={a.n} {a.precision}: {P.info}, launches after fit {ctx.launches()}")
+        return
     print(f"launches before solve {ctx.launches()}", flush=True)
     if a.case == "solve":
         alpha, info = L.laker_pcg_solve(ctx, op, P, dev(inst.y), 1e-6, max_iter=20000, refine_every=20)

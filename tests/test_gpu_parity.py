@@ -279,11 +279,60 @@ def test_map_double_float_matches_oracle(L, ctx, n, d, m):
     A = O.system_matrix(inst.Q, inst.scale, inst.lam)
     alpha = O.solve_direct(A, inst.y)           # large, oscillating coefficients
     op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP32)
-    f = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha)))
+    f = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha), method=L.MAP_DOUBLE_FLOAT))
     fref = O.radio_map(Qg, inst.Q, alpha, inst.scale)
     db = inst.y_sigma * (f - fref)
     assert math.sqrt(np.mean(db ** 2)) < 1e-4
     assert rel(f, fref) < 1e-8
+
+
+@pytest.mark.parametrize("n,d,m,prec", [(1000, 16, 333, 1), (2048, 32, 4096, 2), (777, 64, 1025, 1),
+                                        (100, 32, 70, 2), (4097, 32, 20000, 2), (500, 33, 1000, 1)])
+def test_map_tensor_split_matches_oracle(L, ctx, n, d, m, prec):
+    """The tensor-core map: float64 moments for 1 + L + L^2/2 and tcgen05
+    logits for the remainder L^3 g(L).  Against the float64 oracle map of the
+    same (large, oscillating) alpha: the remainder's float32 errors weigh ~1e-3
+    of a plain float32 map's, so the map stays far inside 0.01 dB (measured on
+    the CPU model of the kernel: ~1e-4 dB at n = 8192).  Ragged m and n (not
+    multiples of 256 and 128), one tile, and d = 16 / 32 / 64 cover the tile
+    shapes; LAKER_MAP_AUTO takes the same path for mixed operators."""
+    from tests.gpu_util import dev, host
+    inst = _inst(n, d, 1e-4, 60 + d, grid=int(math.ceil(math.sqrt(m))))
+    Qg = inst.Qg[:m]
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    alpha = O.solve_direct(A, inst.y)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, prec)
+    f = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha), method=L.MAP_TENSOR))
+    fref = O.radio_map(Qg, inst.Q, alpha, inst.scale)
+    db = inst.y_sigma * (f - fref)
+    assert math.sqrt(np.mean(db ** 2)) < 1e-3, math.sqrt(np.mean(db ** 2))
+    assert np.max(np.abs(db)) < 5e-3
+    auto = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha)))
+    assert np.array_equal(auto, f)
+
+
+def test_map_tensor_split_on_a_float64_operator_and_its_bound(L, ctx):
+    """The split form on request for a float64 operator (the default there is
+    the float64 kernel), and its logit bound: with scale * max|q|^2 > 1/2 the
+    tensor method is refused and AUTO falls back to the double-float kernel."""
+    from tests.gpu_util import dev, host
+    n, d, m = 1500, 32, 2000
+    inst = _inst(n, d, 1e-3, 91, grid=45)
+    Qg = inst.Qg[:m]
+    alpha = O.solve_direct(O.system_matrix(inst.Q, inst.scale, inst.lam), inst.y)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP64)
+    fref = O.radio_map(Qg, inst.Q, alpha, inst.scale)
+    f64 = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha)))
+    assert np.array_equal(f64, host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha), method=L.MAP_DOUBLE_FLOAT)))
+    ft = host(L.laker_eval_map(ctx, op, dev(Qg), dev(alpha), method=L.MAP_TENSOR))
+    assert math.sqrt(np.mean((inst.y_sigma * (ft - fref)) ** 2)) < 1e-3
+    big = 4.0                                     # scale * max|q|^2 ~ 4 * 1.5 > 1/2
+    op2 = L.laker_build_kernel(ctx, dev(inst.Q), big, inst.lam, L.FP32)
+    with pytest.raises(L.LakerError):
+        L.laker_eval_map(ctx, op2, dev(Qg), dev(alpha), method=L.MAP_TENSOR)
+    fa = host(L.laker_eval_map(ctx, op2, dev(Qg), dev(alpha)))
+    fr2 = O.radio_map(Qg, inst.Q, alpha, big)
+    assert np.linalg.norm(fa - fr2) / np.linalg.norm(fr2) < 1e-8
 
 
 @pytest.mark.parametrize("n,d", [(100, 16), (1000, 32), (4097, 32), (777, 64)])

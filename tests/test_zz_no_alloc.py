@@ -4,7 +4,7 @@ Callers that cannot call cudaMalloc -- because another allocator owns the
 device memory, or because they must not synchronise the device -- use this
 entry point; it takes its scratch from a static device array inside the
 library.  These tests call it through the C ABI and check it against the
-ordinary laker_eval_map on the same inputs, twice in a row (the second call
+allocating map with the same (double-float / float64) method on the same inputs, twice in a row (the second call
 runs on the scratch the first one left behind), for a float64 operator and a
 double-float (FP32) one, and check that oversized requests are refused.
 This file is collected last so that a stop-at-first-failure run has already
@@ -40,7 +40,7 @@ def test_noalloc_map_matches_allocating_map_twice(L, precision, n, d, m):
     Qg = dev(inst.Qg[:m])
     for call in range(2):
         alpha = dev(synth.random_vector(n, 100 * call + d) * 1e3)
-        ref = L.laker_eval_map(ctx, op, Qg, alpha).cpu().numpy()
+        ref = L.laker_eval_map(ctx, op, Qg, alpha, method=L.MAP_DOUBLE_FLOAT).cpu().numpy()
         out = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda")
         got = L.laker_eval_map_noalloc(ctx, op, Qg, alpha, out).cpu().numpy()
         assert np.all(np.isfinite(got))
