@@ -663,7 +663,7 @@ laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item
     for (int i = 0; i < count; ++i) {
         nsum += items[i].op->n;
         ldsum += items[i].op->ldk;
-        nrsum += (items[i].P && items[i].P->kind == PRECOND_CCCP) ? items[i].P->n_r : 0;
+        nrsum += (items[i].P && items[i].P->kind == PRECOND_CCCP) ? items[i].P->n_w : 0;
     }
     double* vec = nullptr;
     float* pf = nullptr;
@@ -696,14 +696,14 @@ laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item
         I.K64 = op->K64;
         I.kind = P ? P->kind : PRECOND_IDENTITY;
         if (I.kind == PRECOND_CCCP) {
-            I.n_r = P->n_r;
+            I.n_r = P->n_w;
             I.ldu = P->ldu;
             I.cinv = P->cinvsqrt;
             I.UT = fp64_prec ? (const void*)P->UT64 : (const void*)P->UT32;
             I.W = fp64_prec ? (const void*)P->W64 : (const void*)P->W32;
-            I.ldw = fp64_prec ? P->n_r : P->ldw;
+            I.ldw = fp64_prec ? P->n_w : P->ldw;
             I.t = tv + offt;
-            offt += P->n_r;
+            offt += P->n_w;
         }
         if (I.kind == PRECOND_JACOBI) I.dinv = P->dinv;
         I.y = items[i].y;

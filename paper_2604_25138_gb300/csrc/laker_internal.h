@@ -70,6 +70,7 @@ struct laker_precond {
     int kind = PRECOND_IDENTITY;
     int64_t n = 0;
     int n_r = 0;
+    int n_w = 0;              // columns of the apply form (UT, W): n_r, or the kept eigen-directions
     double c = 1.0;           // Sigma_* = c I + U diag(D) U^T
     double cinvsqrt = 1.0;    // c^{-1/2}
     double* D = nullptr;      // n_r

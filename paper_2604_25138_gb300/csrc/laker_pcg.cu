@@ -634,12 +634,12 @@ PrecView make_view(const laker_precond* P, bool use32) {
     PrecView v{};
     if (P == nullptr) { v.kind = PRECOND_IDENTITY; return v; }
     v.kind = P->kind;
-    v.n_r = P->n_r;
+    v.n_r = P->n_w;
     v.ldu = P->ldu;
     v.cinv = P->cinvsqrt;
     v.UT = use32 ? (const void*)P->UT32 : (const void*)P->UT64;
     v.W = use32 ? (const void*)P->W32 : (const void*)P->W64;
-    v.ldw = use32 ? P->ldw : P->n_r;
+    v.ldw = use32 ? P->ldw : P->n_w;
     v.dinv = P->dinv;
     return v;
 }
@@ -780,7 +780,7 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
     void* t = nullptr;
     double* ra = nullptr;
     laker_status st;
-    if ((st = lk_malloc(ctx, &t, (size_t)P->n_r * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, &t, (size_t)P->n_w * sizeof(double))) != LAKER_OK) return st;
     if (reinterpret_cast<uintptr_t>(r) & 15) {   // the U^T r kernel reads r with 16-byte loads
         if ((st = lk_malloc(ctx, (void**)&ra, (size_t)n * sizeof(double))) != LAKER_OK) { cudaFree(t); return st; }
         LK_CUDA(ctx, cudaMemcpyAsync(ra, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -807,7 +807,7 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     const bool mixed = (op->precision != LAKER_FP64) && refine_every > 0;
     const bool use32 = (op->precision != LAKER_FP64);
     Workspace ws{};
-    laker_status st = ws_alloc(ctx, op, P ? P->n_r : 0, ws);
+    laker_status st = ws_alloc(ctx, op, P ? P->n_w : 0, ws);
     if (st != LAKER_OK) return st;
     PrecView pv = make_view(P, use32);
     if (P && P->kind == PRECOND_CCCP && ((use32 && (P->UT32 == nullptr || P->W32 == nullptr)) ||
