@@ -459,94 +459,156 @@ __device__ __forceinline__ int rr_player(int pos, int round, int m) {
     return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1);
 }
 
+// 1/x for |x| in (1e-30, 1e30): a float32 estimate refined by two Newton
+// steps y <- y (2 - x y) (relative error ~1e-7 -> ~1e-14 -> float64 rounding).
+__device__ __forceinline__ double rcp_newton(double x) {
+    double y = (fabs(x) > 1e-30 && fabs(x) < 1e30) ? (double)__frcp_rn((float)x) : 1.0 / x;
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    return y;
+}
+
 // Rotations of one round of the round-robin pairing: pair k = (p, q), p < q,
-// gets (c, s) that zeroes its 2 x 2 block of S (t = sign(tau) /
-// (|tau| + sqrt(1 + tau^2)), tau = (S_qq - S_pp) / (2 S_pq)).
-__global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double* __restrict__ cs) {
+// gets (c, s) that zeroes its 2 x 2 block of S: t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)), zeta = (S_qq - S_pp) / (2 S_pq), c = 1 / sqrt(1 + t^2),
+// s = t c.  With T32 (mixed operators) t is formed in float32: its accuracy
+// only decides how far the pair's coupling drops (to ~1e-7 of itself), while
+// c and s are float64 from t so that every rotation is orthogonal to float64
+// rounding; otherwise t is float64 from Newton reciprocals and square roots
+// (a float64 division or square root is a long dependent sequence on this
+// GPU; a Newton step is a few FMAs).  A pair keeps the identity (s = 0
+// exactly, which the update skips) when its coupling is negligible, S_pq^2 <=
+// 1e-30 |S_pp S_qq|, or when both diagonal entries are below tau: couplings
+// inside the cluster below tau do not move P (see the sweep loop), so they are
+// left unrotated.
+// The round's non-identity pairs are appended to act[] (count nact[round],
+// zero at the start of the sweep); their order varies between runs but the
+// update does the same arithmetic for each pair whatever its place.
+template <bool T32>
+__global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double tau, double* __restrict__ cs,
+                          int2* __restrict__ pq, int* __restrict__ act, int* __restrict__ nact) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m / 2) return;
     int p = rr_player(k, round, m), q = rr_player(m - 1 - k, round, m);
     if (p > q) { const int t = p; p = q; q = t; }
+    pq[k] = make_int2(p, q);
     const double app = S[(int64_t)p * m + p], aqq = S[(int64_t)q * m + q], apq = S[(int64_t)p * m + q];
     double c = 1.0, s = 0.0;
-    if (apq != 0.0 && fabs(apq) > 1e-300) {
-        const double tau = (aqq - app) / (2.0 * apq);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        c = 1.0 / sqrt(1.0 + t * t);
+    if (apq * apq > 1e-30 * fabs(app * aqq) && fmax(app, aqq) >= tau) {
+        double t;
+        if (T32) {
+            const float a2 = 2.f * (float)apq;
+            const float zeta = (a2 != 0.f) ? (float)(aqq - app) / a2 : INFINITY;
+            t = (double)(copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))));
+        } else {
+            const double zeta = (aqq - app) * rcp_newton(2.0 * apq);
+            const double w = fma(zeta, zeta, 1.0);
+            t = (zeta >= 0.0 ? 1.0 : -1.0) * rcp_newton(fabs(zeta) + w * rsqrt_newton(w));
+        }
+        c = rsqrt_newton(fma(t, t, 1.0));
         s = t * c;
+        if (s == 0.0) c = 1.0;
     }
     cs[2 * k] = c;
     cs[2 * k + 1] = s;
+    if (s != 0.0) act[atomicAdd(nact + round, 1)] = k;
 }
 
-// One round of the two-sided update in a single pass over S and V, from the
-// input buffers into the output buffers.  Thread (i, j) with j >= i (pairs of
-// the round) forms the 2 x 2 block R_i^T S_ij R_j of rows (p_i, q_i) and
-// columns (p_j, q_j) and writes it and its transpose (S stays symmetric; the
-// diagonal blocks become diagonal); threads of the second range rotate the
-// columns (p_j, q_j) of one row of V.  Consecutive threads take consecutive j.
+// One round of the two-sided update, in place, over the round's active
+// (non-identity) pairs act[0..na).  First range, (a, j): the 2 x 2 block
+// R_i^T S_ij R_j of rows (p_i, q_i), i = act[a], and columns (p_j, q_j) of
+// any pair j, written with its transpose (S stays symmetric; the diagonal
+// block becomes diagonal); a block of two active pairs is taken once, from
+// the smaller of the two.  Second range, (row, a): columns (p_i, q_i) of one
+// row of V.  Every element belongs to exactly one block or V pair, so the
+// round has no read-write overlap between threads, and the work shrinks with
+// the number of active pairs.  With exact (float64) angles the rotated
+// coupling of the diagonal block is set to zero; with float32 angles it keeps
+// its computed residual, so that S stays V^T S_0 V to float64 rounding.
 __global__ void __launch_bounds__(256)
-k_jac_update(const double* __restrict__ Sin, double* __restrict__ Sout, const double* __restrict__ Vin,
-             double* __restrict__ Vout, int m, int round, const double* __restrict__ cs) {
+k_jac_update(double* __restrict__ S, double* __restrict__ V, int m, int round, const double* __restrict__ cs,
+             const int2* __restrict__ pq, const int* __restrict__ act, const int* __restrict__ nact, int exact) {
     const int half = m / 2;
-    const int64_t ns = (int64_t)half * half, total = ns + (int64_t)m * half;
+    const int na = nact[round];
+    const int64_t nsS = (int64_t)na * half, total = nsS + (int64_t)na * m;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        if (e < ns) {
-            const int i = (int)(e / half), j = (int)(e % half);
-            if (j < i) continue;
-            int pi = rr_player(i, round, m), qi = rr_player(m - 1 - i, round, m);
-            if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-            int pj = rr_player(j, round, m), qj = rr_player(m - 1 - j, round, m);
-            if (pj > qj) { const int t = pj; pj = qj; qj = t; }
-            const double ci = cs[2 * i], si = cs[2 * i + 1], cj = cs[2 * j], sj = cs[2 * j + 1];
-            const double a = Sin[(int64_t)pi * m + pj], b = Sin[(int64_t)pi * m + qj];
-            const double c = Sin[(int64_t)qi * m + pj], d = Sin[(int64_t)qi * m + qj];
-            const double r0a = ci * a - si * c, r0b = ci * b - si * d;
-            const double r1a = si * a + ci * c, r1b = si * b + ci * d;
+        if (e < nsS) {
+            const int a = (int)(e / half), j = (int)(e - (int64_t)a * half);
+            const int i = act[a];
+            const double si = cs[2 * i + 1], sj = cs[2 * j + 1];
+            if (sj != 0.0 && j < i) continue;   // taken from row j
+            const double ci = cs[2 * i], cj = cs[2 * j];
+            const int2 PI = pq[i], PJ = pq[j];
+            const int64_t rp = (int64_t)PI.x * m, rq = (int64_t)PI.y * m;
+            const double a0 = S[rp + PJ.x], b0 = S[rp + PJ.y];
+            const double c0 = S[rq + PJ.x], d0 = S[rq + PJ.y];
+            const double r0a = ci * a0 - si * c0, r0b = ci * b0 - si * d0;
+            const double r1a = si * a0 + ci * c0, r1b = si * b0 + ci * d0;
             double o00 = cj * r0a - sj * r0b, o01 = sj * r0a + cj * r0b;
             double o10 = cj * r1a - sj * r1b, o11 = sj * r1a + cj * r1b;
             if (i == j) {
-                o01 = 0.0;
-                o10 = 0.0;
+                if (exact) o01 = 0.0;
+                o10 = o01;
             }
-            Sout[(int64_t)pi * m + pj] = o00;
-            Sout[(int64_t)pi * m + qj] = o01;
-            Sout[(int64_t)qi * m + pj] = o10;
-            Sout[(int64_t)qi * m + qj] = o11;
+            S[rp + PJ.x] = o00;
+            S[rp + PJ.y] = o01;
+            S[rq + PJ.x] = o10;
+            S[rq + PJ.y] = o11;
             if (i != j) {
-                Sout[(int64_t)pj * m + pi] = o00;
-                Sout[(int64_t)qj * m + pi] = o01;
-                Sout[(int64_t)pj * m + qi] = o10;
-                Sout[(int64_t)qj * m + qi] = o11;
+                S[(int64_t)PJ.x * m + PI.x] = o00;
+                S[(int64_t)PJ.y * m + PI.x] = o01;
+                S[(int64_t)PJ.x * m + PI.y] = o10;
+                S[(int64_t)PJ.y * m + PI.y] = o11;
             }
         } else {
-            const int64_t f = e - ns;
-            const int row = (int)(f / half), j = (int)(f % half);
-            int pj = rr_player(j, round, m), qj = rr_player(m - 1 - j, round, m);
-            if (pj > qj) { const int t = pj; pj = qj; qj = t; }
-            const double cj = cs[2 * j], sj = cs[2 * j + 1];
-            const double va = Vin[(int64_t)row * m + pj], vb = Vin[(int64_t)row * m + qj];
-            Vout[(int64_t)row * m + pj] = cj * va - sj * vb;
-            Vout[(int64_t)row * m + qj] = sj * va + cj * vb;
+            const int64_t f = e - nsS;
+            const int row = (int)(f / na), a = (int)(f - (int64_t)row * na);
+            const int i = act[a];
+            const double si = cs[2 * i + 1], ci = cs[2 * i];
+            const int2 PI = pq[i];
+            double* vr = V + (int64_t)row * m;
+            const double va = vr[PI.x], vb = vr[PI.y];
+            vr[PI.x] = ci * va - si * vb;
+            vr[PI.y] = si * va + ci * vb;
         }
     }
 }
 
-// Squared Frobenius norms (single block): out[0] off-diagonal, out[1] total,
-// out[2] off-diagonal entries S_pq with max(S_pp, S_qq) >= tau (the couplings
-// that move P: inside the cluster below tau, phi(l) = (c + l)^-1/2 - c^-1/2 is
-// linear in l and needs no diagonalisation).
-__global__ void k_offdiag(const double* __restrict__ S, int m, double tau, double* out) {
+// Squared Frobenius norms of S, per row (block per row; diag = diag(S)):
+// part[3 row] off-diagonal, part[3 row + 1] all, part[3 row + 2] off-diagonal
+// entries S_pq with max(S_pp, S_qq) >= tau (the couplings that move P: inside
+// the cluster below tau, phi(l) = (c + l)^-1/2 - c^-1/2 is linear in l and
+// needs no diagonalisation).  k_offdiag_sum adds the rows in a fixed order.
+__global__ void k_offdiag_rows(const double* __restrict__ S, const double* __restrict__ diag, int m, double tau,
+                               double* __restrict__ part) {
+    __shared__ double red[32];
+    const int p = blockIdx.x;
+    const double dp = diag[p];
+    double off = 0.0, tot = 0.0, rel = 0.0;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const double v = S[(int64_t)p * m + q];
+        tot = fma(v, v, tot);
+        if (q != p) {
+            off = fma(v, v, off);
+            if (fmax(dp, diag[q]) >= tau) rel = fma(v, v, rel);
+        }
+    }
+    off = lk::block_sum(off, red);
+    tot = lk::block_sum(tot, red);
+    rel = lk::block_sum(rel, red);
+    if (threadIdx.x == 0) {
+        part[3 * p] = off;
+        part[3 * p + 1] = tot;
+        part[3 * p + 2] = rel;
+    }
+}
+__global__ void k_offdiag_sum(const double* __restrict__ part, int m, double* out) {
     __shared__ double red[32];
     double off = 0.0, tot = 0.0, rel = 0.0;
-    for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
-        const double v = S[idx];
-        tot = fma(v, v, tot);
-        const int64_t p = idx / m, q = idx % m;
-        if (p != q) {
-            off = fma(v, v, off);
-            if (fmax(S[p * m + p], S[q * m + q]) >= tau) rel = fma(v, v, rel);
-        }
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        off += part[3 * p];
+        tot += part[3 * p + 1];
+        rel += part[3 * p + 2];
     }
     off = lk::block_sum(off, red);
     tot = lk::block_sum(tot, red);
@@ -747,6 +809,13 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     if ((st = lk_malloc(ctx, (void**)&Sm, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&V, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&cs, (size_t)m * sizeof(double))) != LAKER_OK) return st;
+    int2* pq = nullptr;   // the round's pairs (p, q), p < q
+    int *act = nullptr, *nact = nullptr;   // the round's active pairs and their count per round
+    if ((st = lk_malloc(ctx, (void**)&act, (size_t)(m / 2) * sizeof(int))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&nact, (size_t)m * sizeof(int))) != LAKER_OK) return st;
+    double* opart = nullptr;   // per-row squared norms of S
+    if ((st = lk_malloc(ctx, (void**)&pq, (size_t)(m / 2) * sizeof(int2))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&opart, (size_t)3 * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&X, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&B0, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&B, (size_t)nr * nr * sizeof(double))) != LAKER_OK) return st;
@@ -755,30 +824,28 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     LK_LAUNCHED(ctx);
     k_eye<<<gsz((int64_t)m * m), 256, 0, s>>>(V, m);
     LK_LAUNCHED(ctx);
-    // One sweep = m - 1 rounds, each a rotation kernel and one fused update pass
-    // from one buffer pair into the other.  m - 1 is odd, so sweeps alternate
-    // between starting from (Sm, V) and from (S2, V2): two graphs.
-    double *S2 = nullptr, *V2 = nullptr;
-    if ((st = lk_malloc(ctx, (void**)&S2, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
-    if ((st = lk_malloc(ctx, (void**)&V2, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
+    // One sweep = m - 1 rounds, each a rotation kernel and one in-place update
+    // pass, captured once as a graph.
     const double tau = (op->precision == LAKER_FP64) ? 0.0 : 1e-2 * h.c;
+    const double tau_rot = (op->precision == LAKER_FP64) ? -HUGE_VAL : tau;   // float64: rotate every pair
     const int64_t upd_work = (int64_t)(m / 2) * (m / 2) + (int64_t)m * (m / 2);
     const unsigned upd_blocks = (unsigned)std::min<int64_t>((upd_work + 255) / 256, 8 * ctx->num_sms);
-    cudaGraph_t gr[2] = {nullptr, nullptr};
-    cudaGraphExec_t ge[2] = {nullptr, nullptr};
-    for (int start = 0; start < 2; ++start) {
-        LK_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        double *Sa = start ? S2 : Sm, *Sb = start ? Sm : S2, *Va = start ? V2 : V, *Vb = start ? V : V2;
-        for (int r = 0; r < m - 1; ++r) {
-            k_jac_rot<<<(unsigned)((m / 2 + 127) / 128), 128, 0, s>>>(Sa, m, r, cs);
-            k_jac_update<<<upd_blocks, 256, 0, s>>>(Sa, Sb, Va, Vb, m, r, cs);
-            std::swap(Sa, Sb);
-            std::swap(Va, Vb);
-        }
-        k_offdiag<<<1, 1024, 0, s>>>(Sa, m, tau, nrm);
-        LK_CUDA(ctx, cudaStreamEndCapture(s, &gr[start]));
-        LK_CUDA(ctx, cudaGraphInstantiate(&ge[start], gr[start], 0));
+    double* dg = tmpv;   // diag(S) for the norms (free scratch, 4 NP doubles)
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    LK_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    LK_CUDA(ctx, cudaMemsetAsync(nact, 0, (size_t)m * sizeof(int), s));
+    for (int r = 0; r < m - 1; ++r) {
+        const unsigned rb = (unsigned)((m / 2 + 31) / 32);
+        if (op->precision == LAKER_FP64) k_jac_rot<false><<<rb, 32, 0, s>>>(Sm, m, r, tau_rot, cs, pq, act, nact);
+        else k_jac_rot<true><<<rb, 32, 0, s>>>(Sm, m, r, tau_rot, cs, pq, act, nact);
+        k_jac_update<<<upd_blocks, 256, 0, s>>>(Sm, V, m, r, cs, pq, act, nact, op->precision == LAKER_FP64);
     }
+    k_diag_copy<<<gsz(m), 256, 0, s>>>(m, Sm, dg);
+    k_offdiag_rows<<<(unsigned)m, 256, 0, s>>>(Sm, dg, m, tau, opart);
+    k_offdiag_sum<<<1, 1024, 0, s>>>(opart, m, nrm);
+    LK_CUDA(ctx, cudaStreamEndCapture(s, &gr));
+    LK_CUDA(ctx, cudaGraphInstantiate(&ge, gr, 0));
     // Stop once the off-diagonal Frobenius norm is below 1e-12 of the matrix
     // norm, or after 12 sweeps.  For float32 and split-bf16 operators, whose
     // solves are judged by the true residual, also once the couplings that
@@ -786,31 +853,21 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     // coupling e changes P = Sigma^-1/2 by at most e / (2 c) relative, and
     // inside the cluster below c/100 the factor phi(l) is linear in l up to
     // (3/4)(l/c) relative, so P stays within a few % of Sigma_*^-1/2 along
-    // every direction and positive definite.
+    // every direction and positive definite.  For the same reason the
+    // rotations of those operators leave couplings inside that cluster alone.
     double hn[3] = {0, 0, 0};
     int sweeps = 0;
     const double off_stop = (op->precision == LAKER_FP64) ? 0.0 : 2.5e-3 * h.c * h.c;
-    int cur = 0;   // 0: the latest S, V are in (Sm, V); 1: in (S2, V2)
     for (int sweep = 0; sweep < 12; ++sweep) {
-        LK_CUDA(ctx, cudaGraphLaunch(ge[cur], s));
-        cur ^= 1;
-        ctx->launches += 2 * (m - 1) + 1;
+        LK_CUDA(ctx, cudaGraphLaunch(ge, s));
+        ctx->launches += 2 * (m - 1) + 3;
         ++sweeps;
         LK_CUDA(ctx, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, s));
         LK_CUDA(ctx, cudaStreamSynchronize(s));
         if (!(hn[0] > 1e-24 * hn[1]) || !(hn[2] > off_stop)) break;
     }
-    for (int k = 0; k < 2; ++k) {
-        cudaGraphExecDestroy(ge[k]);
-        cudaGraphDestroy(gr[k]);
-    }
-    if (cur == 1) {   // bring the result back to (Sm, V)
-        LK_CUDA(ctx, cudaMemcpyAsync(Sm, S2, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        LK_CUDA(ctx, cudaMemcpyAsync(V, V2, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    }
-    LK_CUDA(ctx, cudaStreamSynchronize(s));
-    cudaFree(S2);
-    cudaFree(V2);
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(gr);
     P->kind = PRECOND_CCCP;
     P->n = n;
     P->n_r = nr;
@@ -886,7 +943,8 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     }
     LK_CUDA(ctx, cudaStreamSynchronize(s));
     for (void* ptr : {(void*)tmpv, (void*)M, (void*)A, (void*)D, (void*)Dn, (void*)q, (void*)partials, (void*)cn,
-                      (void*)dst, (void*)Sm, (void*)V, (void*)cs, (void*)X, (void*)B0, (void*)B, (void*)nrm, (void*)dinv})
+                      (void*)dst, (void*)Sm, (void*)V, (void*)cs, (void*)X, (void*)B0, (void*)B, (void*)nrm, (void*)dinv, (void*)pq, (void*)opart, (void*)act,
+                      (void*)nact})
         cudaFree(ptr);
     if (info) {
         info->iterations = h.iter;
