@@ -485,14 +485,14 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // zero at the start of the sweep); their order varies between runs but the
 // update does the same arithmetic for each pair whatever its place.
 template <bool T32>
-__global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double tau, double* __restrict__ cs,
-                          int2* __restrict__ pq, int* __restrict__ act, int* __restrict__ nact) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m / 2) return;
+__device__ __forceinline__ void jac_rotation(const double* __restrict__ S, int m, int round, int k, double tau,
+                                             double* __restrict__ cs, int2* __restrict__ pq, int* __restrict__ act,
+                                             int* __restrict__ nact) {
     int p = rr_player(k, round, m), q = rr_player(m - 1 - k, round, m);
     if (p > q) { const int t = p; p = q; q = t; }
     pq[k] = make_int2(p, q);
-    const double app = S[(int64_t)p * m + p], aqq = S[(int64_t)q * m + q], apq = S[(int64_t)p * m + q];
+    const double app = __ldcg(S + (int64_t)p * m + p), aqq = __ldcg(S + (int64_t)q * m + q);
+    const double apq = __ldcg(S + (int64_t)p * m + q);
     double c = 1.0, s = 0.0;
     if (apq * apq > 1e-30 * fabs(app * aqq) && fmax(app, aqq) >= tau) {
         double t;
@@ -513,6 +513,12 @@ __global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double
     cs[2 * k + 1] = s;
     if (s != 0.0) act[atomicAdd(nact + round, 1)] = k;
 }
+template <bool T32>
+__global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double tau, double* __restrict__ cs,
+                          int2* __restrict__ pq, int* __restrict__ act, int* __restrict__ nact) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m / 2) jac_rotation<T32>(S, m, round, k, tau, cs, pq, act, nact);
+}
 
 // One round of the two-sided update, in place, over the round's active
 // (non-identity) pairs act[0..na).  First range, (a, j): the 2 x 2 block
@@ -525,9 +531,13 @@ __global__ void k_jac_rot(const double* __restrict__ S, int m, int round, double
 // the number of active pairs.  With exact (float64) angles the rotated
 // coupling of the diagonal block is set to zero; with float32 angles it keeps
 // its computed residual, so that S stays V^T S_0 V to float64 rounding.
+// (Forming the next round's rotations in the last block to finish, instead
+// of a separate launch, measured slower: 16.3 us against 8.5 + 4.5 us.)
+template <bool T32>
 __global__ void __launch_bounds__(256)
 k_jac_update(double* __restrict__ S, double* __restrict__ V, int m, int round, const double* __restrict__ cs,
-             const int2* __restrict__ pq, const int* __restrict__ act, const int* __restrict__ nact, int exact) {
+             const int2* __restrict__ pq, const int* __restrict__ act, const int* __restrict__ nact) {
+    constexpr bool exact = !T32;
     const int half = m / 2;
     const int na = nact[round];
     const int64_t nsS = (int64_t)na * half, total = nsS + (int64_t)na * m;
@@ -813,6 +823,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     int *act = nullptr, *nact = nullptr;   // the round's active pairs and their count per round
     if ((st = lk_malloc(ctx, (void**)&act, (size_t)(m / 2) * sizeof(int))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&nact, (size_t)m * sizeof(int))) != LAKER_OK) return st;
+
     double* opart = nullptr;   // per-row squared norms of S
     if ((st = lk_malloc(ctx, (void**)&pq, (size_t)(m / 2) * sizeof(int2))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&opart, (size_t)3 * m * sizeof(double))) != LAKER_OK) return st;
@@ -835,11 +846,16 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     cudaGraphExec_t ge = nullptr;
     LK_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     LK_CUDA(ctx, cudaMemsetAsync(nact, 0, (size_t)m * sizeof(int), s));
+    const unsigned rb = (unsigned)((m / 2 + 31) / 32);
+    const bool f64 = op->precision == LAKER_FP64;
     for (int r = 0; r < m - 1; ++r) {
-        const unsigned rb = (unsigned)((m / 2 + 31) / 32);
-        if (op->precision == LAKER_FP64) k_jac_rot<false><<<rb, 32, 0, s>>>(Sm, m, r, tau_rot, cs, pq, act, nact);
-        else k_jac_rot<true><<<rb, 32, 0, s>>>(Sm, m, r, tau_rot, cs, pq, act, nact);
-        k_jac_update<<<upd_blocks, 256, 0, s>>>(Sm, V, m, r, cs, pq, act, nact, op->precision == LAKER_FP64);
+        if (f64) {
+            k_jac_rot<false><<<rb, 32, 0, s>>>(Sm, m, r, tau_rot, cs, pq, act, nact);
+            k_jac_update<false><<<upd_blocks, 256, 0, s>>>(Sm, V, m, r, cs, pq, act, nact);
+        } else {
+            k_jac_rot<true><<<rb, 32, 0, s>>>(Sm, m, r, tau_rot, cs, pq, act, nact);
+            k_jac_update<true><<<upd_blocks, 256, 0, s>>>(Sm, V, m, r, cs, pq, act, nact);
+        }
     }
     k_diag_copy<<<gsz(m), 256, 0, s>>>(m, Sm, dg);
     k_offdiag_rows<<<(unsigned)m, 256, 0, s>>>(Sm, dg, m, tau, opart);

@@ -400,15 +400,18 @@ k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ row
     const int64_t i = (int64_t)I * MF_B + c;
     double pw = 0.0;
     if (grp == 0 && i < n) {
-        double tot = 0.0;
+        // four independent chains of four, added in a fixed order
+        double q4[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int gq = 0; gq < MF_FIN_GROUPS; ++gq) tot += (double)gsum[gq][threadIdx.x];
+        for (int gq = 0; gq < MF_FIN_GROUPS; ++gq) q4[gq & 3] += (double)gsum[gq][threadIdx.x];
+        const double tot = (q4[0] + q4[1]) + (q4[2] + q4[3]);
         const double wi = fma(lambda, p[i], tot);
         w[i] = wi;
         pw = p[i] * wi;
     }
     if (sc == nullptr) return;
-    pw = lk::block_sum(pw, red);
+    // only group 0 (warp 0) holds nonzero terms: one warp reduces them
+    if (grp == 0) pw = lk::warp_sum(pw);
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) partials[bid] = pw;
     if (lk::last_block(&sc->ticket[0])) {

@@ -241,6 +241,7 @@ __device__ __forceinline__ void row_range(int64_t n, int64_t& r0, int64_t& r1) {
 struct PrecView {
     int kind;
     int n_r;
+    int nch;          // row chunks of U^T r: t holds nch partial vectors of n_r
     int ldw;          // row pitch of W (n_r rounded up to 4 for float32 W, n_r for float64)
     int64_t ldu;
     double cinv;
@@ -383,9 +384,11 @@ __device__ __forceinline__ float dot_v(const float4& u, const float* rv) {
 }
 __device__ __forceinline__ double dot_v(const double2& u, const double* rv) { return fma(u.x, rv[0], u.y * rv[1]); }
 
-// UTR: t_k = sum_i U_ik r_i for four directions k0..k0+3 per block: every load
-// of r serves the four rows of U^T (padded pitch ldu, zeros past n), 16-byte
-// loads, two steps in flight; each block reduces its four sums in a fixed order.
+// UTR: t_k = sum_i U_ik r_i for four directions k0..k0+3 per block and one
+// chunk of the rows per blockIdx.y (partial sums t[chunk * n_r + k], added in
+// chunk order by the apply): every load of r serves the four rows of U^T
+// (padded pitch ldu, zeros past n), 16-byte loads, two steps in flight; each
+// block reduces its four sums in a fixed order.
 template <typename PT>
 __global__ void __launch_bounds__(256)
 k_utr(int64_t n, PrecView pv, const double* __restrict__ r, PT* __restrict__ t, const PcgScalars* sc, int gate) {
@@ -399,9 +402,11 @@ k_utr(int64_t n, PrecView pv, const double* __restrict__ r, PT* __restrict__ t, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[q] = reinterpret_cast<const V*>((const PT*)pv.UT + (int64_t)(k0 + (q < nk ? q : 0)) * pv.ldu);
     const int64_t nfull = n / VN;                 // vectors entirely inside [0, n)
+    const int64_t per = (nfull + gridDim.y - 1) / gridDim.y;
+    const int64_t v_lo = min(nfull, (int64_t)blockIdx.y * per), v_hi = min(nfull, v_lo + per);
     PT a[4] = {PT(0), PT(0), PT(0), PT(0)}, b[4] = {PT(0), PT(0), PT(0), PT(0)};
-    int64_t v = threadIdx.x;
-    for (; v + 256 < nfull; v += 512) {
+    int64_t v = v_lo + threadIdx.x;
+    for (; v + 256 < v_hi; v += 512) {
         PT ra[VN], rb[VN];
         load_r<PT>(r, v * VN, ra);
         load_r<PT>(r, (v + 256) * VN, rb);
@@ -411,15 +416,16 @@ k_utr(int64_t n, PrecView pv, const double* __restrict__ r, PT* __restrict__ t, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) { a[q] += dot_v(ua[q], ra); b[q] += dot_v(ub[q], rb); }
     }
-    for (; v < nfull; v += 256) {
+    for (; v < v_hi; v += 256) {
         PT ra[VN];
         load_r<PT>(r, v * VN, ra);
 #pragma unroll
         for (int q = 0; q < 4; ++q) a[q] += dot_v(__ldg(u[q] + v), ra);
     }
-    for (int64_t i = nfull * VN + threadIdx.x; i < n; i += 256)
+    if (blockIdx.y == gridDim.y - 1)
+        for (int64_t i = nfull * VN + threadIdx.x; i < n; i += 256)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] += reinterpret_cast<const PT*>(u[q])[i] * (PT)r[i];
+            for (int q = 0; q < 4; ++q) b[q] += reinterpret_cast<const PT*>(u[q])[i] * (PT)r[i];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -430,7 +436,7 @@ k_utr(int64_t n, PrecView pv, const double* __restrict__ r, PT* __restrict__ t, 
     if (threadIdx.x < nk) {
         PT s = PT(0);
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
-        t[k0 + threadIdx.x] = s;
+        t[(int64_t)blockIdx.y * pv.n_r + k0 + threadIdx.x] = s;
     }
 }
 
@@ -448,7 +454,12 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
     double rz = 0.0;
     if (pv.kind == PRECOND_CCCP && sizeof(PT) == 4) {
         // float32 W with a 16-byte row pitch: four rows per warp, float4 loads
-        for (int k = threadIdx.x; k < pv.ldw; k += blockDim.x) ts[k] = (k < pv.n_r) ? __ldcg(t + k) : PT(0);
+        for (int k = threadIdx.x; k < pv.ldw; k += blockDim.x) {
+            PT v = PT(0);
+            if (k < pv.n_r)
+                for (int c = 0; c < pv.nch; ++c) v += __ldcg(t + (int64_t)c * pv.n_r + k);
+            ts[k] = v;
+        }
         __syncthreads();
         const float4* W4 = reinterpret_cast<const float4*>(pv.W);
         const float4* t4 = reinterpret_cast<const float4*>(ts);
@@ -481,18 +492,25 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
                     acc[q] = fmaf(w.x, tk.x, fmaf(w.y, tk.y, fmaf(w.z, tk.z, fmaf(w.w, tk.w, acc[q]))));
                 }
             }
+            // every lane holds the four sums; lane q finishes row i + q, so the
+            // float64 tail is one warp instruction per step for all four rows
+            float aq[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float a = lk::warp_sum(acc[q]);
-                if (lane == 0 && q < nrow) {
-                    const double zi = fma(pv.cinv, r[i + q], (double)a);
-                    z[i + q] = zi;
-                    rz = fma(r[i + q], zi, rz);
-                }
+            for (int q = 0; q < 4; ++q) aq[q] = lk::warp_sum(acc[q]);
+            if (lane < nrow) {
+                const float a = (lane == 0) ? aq[0] : (lane == 1) ? aq[1] : (lane == 2) ? aq[2] : aq[3];
+                const double ri = r[i + lane];
+                const double zi = fma(pv.cinv, ri, (double)a);
+                z[i + lane] = zi;
+                rz = fma(ri, zi, rz);
             }
         }
     } else if (pv.kind == PRECOND_CCCP) {
-        for (int k = threadIdx.x; k < pv.n_r; k += blockDim.x) ts[k] = __ldcg(t + k);
+        for (int k = threadIdx.x; k < pv.n_r; k += blockDim.x) {
+            PT v = PT(0);
+            for (int c = 0; c < pv.nch; ++c) v += __ldcg(t + (int64_t)c * pv.n_r + k);
+            ts[k] = v;
+        }
         __syncthreads();
         const PT* W = (const PT*)pv.W;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -630,11 +648,21 @@ laker_status launch_mv_df(laker_ctx* ctx, const laker_op* op, const double* x, d
     return LAKER_OK;
 }
 
-PrecView make_view(const laker_precond* P, bool use32) {
+// Row chunks of U^T r: enough blocks for ~3 per SM, each chunk >= 1024 rows.
+int utr_chunks(const laker_ctx* ctx, int64_t n, int n_w) {
+    const int64_t nb = std::max(1, (n_w + 3) / 4);
+    const int64_t want = (3 * ctx->num_sms + nb - 1) / nb;
+    const int64_t cap = std::max<int64_t>(1, n / 1024);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, cap), 32));
+}
+
+PrecView make_view(const laker_ctx* ctx, const laker_precond* P, bool use32) {
     PrecView v{};
+    v.nch = 1;
     if (P == nullptr) { v.kind = PRECOND_IDENTITY; return v; }
     v.kind = P->kind;
     v.n_r = P->n_w;
+    if (v.kind == PRECOND_CCCP) v.nch = utr_chunks(ctx, P->n, v.n_r);
     v.ldu = P->ldu;
     v.cinv = P->cinvsqrt;
     v.UT = use32 ? (const void*)P->UT32 : (const void*)P->UT64;
@@ -648,7 +676,7 @@ template <typename PT>
 laker_status launch_utr(laker_ctx* ctx, int64_t n, const PrecView& pv, const double* r, PT* t, const PcgScalars* sc,
                         int gate) {
     if (pv.kind != PRECOND_CCCP) return LAKER_OK;
-    k_utr<PT><<<(unsigned)((pv.n_r + 3) / 4), 256, 0, ctx->stream>>>(n, pv, r, t, sc, gate);
+    k_utr<PT><<<dim3((unsigned)((pv.n_r + 3) / 4), (unsigned)pv.nch), 256, 0, ctx->stream>>>(n, pv, r, t, sc, gate);
     LK_LAUNCHED(ctx);
     return LAKER_OK;
 }
@@ -667,7 +695,7 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
     const int64_t nb = std::max<int64_t>(8 * ctx->num_sms + 8, 4 * ((n + 127) / 128) + 8);
     if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
     const int nr = std::max(1, n_r);
-    if ((st = lk_malloc(ctx, &ws.t, (size_t)nr * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, &ws.t, (size_t)nr * utr_chunks(ctx, n, nr) * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&ws.sc, sizeof(PcgScalars))) != LAKER_OK) return st;
     LK_CUDA(ctx, cudaMemsetAsync(ws.sc, 0, sizeof(PcgScalars), ctx->stream));
     ws.ticket = ws.sc->ticket + 7;
@@ -771,7 +799,7 @@ laker_status pcg_prepare(laker_ctx* ctx) {
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z) {
     const int64_t n = P->n;
     const int vb = pre_blocks_for(ctx, n);
-    PrecView pv = make_view(P, P->use32);
+    PrecView pv = make_view(ctx, P, P->use32);
     if (P->kind != PRECOND_CCCP) {
         k_precond<double><<<vb, VEC_THREADS, 0, ctx->stream>>>(n, r, z, nullptr, nullptr, pv, nullptr, GATE_NONE);
         LK_LAUNCHED(ctx);
@@ -780,7 +808,7 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
     void* t = nullptr;
     double* ra = nullptr;
     laker_status st;
-    if ((st = lk_malloc(ctx, &t, (size_t)P->n_w * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, &t, (size_t)P->n_w * pv.nch * sizeof(double))) != LAKER_OK) return st;
     if (reinterpret_cast<uintptr_t>(r) & 15) {   // the U^T r kernel reads r with 16-byte loads
         if ((st = lk_malloc(ctx, (void**)&ra, (size_t)n * sizeof(double))) != LAKER_OK) { cudaFree(t); return st; }
         LK_CUDA(ctx, cudaMemcpyAsync(ra, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -809,7 +837,7 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     Workspace ws{};
     laker_status st = ws_alloc(ctx, op, P ? P->n_w : 0, ws);
     if (st != LAKER_OK) return st;
-    PrecView pv = make_view(P, use32);
+    PrecView pv = make_view(ctx, P, use32);
     if (P && P->kind == PRECOND_CCCP && ((use32 && (P->UT32 == nullptr || P->W32 == nullptr)) ||
                                           (!use32 && P->UT64 == nullptr))) {
         ws_free(ws);
