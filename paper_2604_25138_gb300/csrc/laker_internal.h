@@ -35,6 +35,7 @@ struct laker_ctx {
     bool owns_stream = false;
     int num_sms = 0;
     int64_t launches = 0;
+    void* cublas = nullptr;     // cuBLAS handle for the fit's plain products, created on first use
     std::string last_error;
 };
 
@@ -117,6 +118,7 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
                        int refine_every, laker_solve_info* info);
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
 // laker_fit.cu
+void release_cublas(laker_ctx* ctx);
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
                       double gamma, double rho, double eps, int max_iter, double tol,
                       laker_precond* P, laker_fit_info* info,
