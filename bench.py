@@ -23,6 +23,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -77,7 +78,8 @@ class ClockSampler:
     def __init__(self, device: int):
         self.proc = None
         self.device = device
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        where = os.environ.get("LAKER_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(where, f"laker_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -906,7 +906,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     LK_CUDA(ctx, cudaGraphInstantiate(&ge, gr, 0));
     // Stop once the off-diagonal Frobenius norm is below 1e-12 of the matrix
     // norm, or after 12 sweeps.  For float32 and split-bf16 operators, whose
-    // solves are judged by the true residual, also once the couplings that
+    // solves stop on the true residual, also once the couplings that
     // involve a diagonal entry >= c/100 weigh at most c/20: an unrotated
     // coupling e changes P = Sigma^-1/2 by at most e / (2 c) relative, and
     // inside the cluster below c/100 the factor phi(l) is linear in l up to
