@@ -12,9 +12,12 @@
 // P = Sigma_*^-1/2 = c^-1/2 I + U B U^T with
 //        B = D^1/2 V diag(f(Lambda)) V^T D^1/2,  D^1/2 M D^1/2 = V Lambda V^T,
 //        f(l) = ((c + l)^-1/2 - c^-1/2) / l  (evaluated without cancellation),
-// found by a parallel cyclic Jacobi eigensolver; the apply uses W = U B.
-// All small dense algebra is float64 and spread over many thread blocks (GB300's
-// float64 pipe is slow per SM); every reduction has a fixed order.
+// found by a parallel cyclic Jacobi eigensolver (round-robin rounds, in place,
+// over each round's active pairs); float64 operators apply W = U B, mixed ones
+// the orthonormal form c^-1/2 I + U~ diag(phi) U~^T over the eigen-directions
+// that move P.  All small dense algebra is float64 and spread over many
+// thread blocks (GB300's float64 pipe is slow per SM); every reduction has a
+// fixed order.
 #include <cublas_v2.h>
 
 #include <algorithm>

@@ -1,7 +1,10 @@
 // Radio-map reconstruction  r(x_m) = sum_i exp(scale <q(x_m), q_i>) alpha_i
 // (Sec. III-A, Eq. sc-radio-map-reconstruction; Algorithm 1, reconstruction stage).
 //
-// Block = 64 query rows x one slice of the training points; logits in float64,
+// This file holds the float64 kernel (float64 operators) and the double-float
+// kernel (mixed operators whose logits exceed the tensor-core form's bound, see
+// laker_map_tc.cu), and the dispatch between the methods.  Float64 kernel:
+// block = 64 query rows x one slice of the training points; logits in float64,
 // float64 exp, per-row sums across the 16 column threads by shuffles, slices
 // summed afterwards in a fixed order.
 #include <algorithm>

@@ -2,23 +2,27 @@
 // q' = q sqrt(scale log2 e)  (Sec. III-A Eq. sc-exp-kernel; the matvec-only
 // access of Sec. IV-D, remark after Eq. kernel_shrinkage_cccp_normalization).
 //
-// Blackwell (sm_103a) kernel, one CTA per (128-row block, slice of columns):
-//   * TMA (cp.async.bulk.tensor) streams 128-row tiles of the split-bf16
-//     operands q' = hi + lo into a 4-stage shared-memory ring;
+// Blackwell (sm_103a) kernel over the symmetric tile schedule (each unordered
+// pair of 128-index blocks once, n(n+1)/2 pairs), one persistent CTA per SM
+// on an equal contiguous range of the tiles:
+//   * a TMA (cp.async.bulk.tensor) warp streams the 128-row tiles of block J
+//     (split-bf16 operands q' = hi + lo) through an 8-stage shared-memory ring
+//     (4 stages for d > 32) and reloads the fixed block I once per segment;
 //   * one elected thread issues tcgen05.mma (kind::f16, bf16 in, f32 out) for
 //     the split product  hi_i.hi_j + hi_i.lo_j + lo_i.hi_j + lo_i.lo_j  into a
-//     double-buffered 128 x 128 float32 accumulator in tensor memory.  The
-//     fourth product makes the logits the exact Gram matrix of the rounded
-//     embedding hi + lo, so the computed kernel is exp of a Gram matrix and
-//     stays positive semidefinite (Schur product theorem): without it the
-//     operator error (~1e-6 n) exceeds lambda at n = 16384 and CG breaks down;
-//   * eight epilogue warps read the logits with tcgen05.ld, apply ex2.approx
-//     (the MUFU unit, 32 results/clk/SM on GB300) and accumulate e * p_j in
-//     registers, overlapping the tensor-core work of the next tile.
-// The grid is one wave of persistent CTAs (two per SM) over equal contiguous
-// ranges of the row-block-major tile order; per-segment row sums go to a
-// partial buffer and a finishing kernel adds lambda p, sums a row's partials
-// in a fixed order and performs the PCG p^T w reduction.
+//     ring of four 128 x 128 float32 accumulators (all 512 tensor-memory
+//     columns).  The fourth product makes the logits the exact Gram matrix of
+//     the rounded embedding hi + lo, so the computed kernel is exp of a Gram
+//     matrix and stays positive semidefinite (Schur product theorem): without
+//     it the operator error (~1e-6 n) exceeds lambda at n = 16384 and CG
+//     breaks down;
+//   * sixteen epilogue warps read the logits with tcgen05.ld, apply ex2.approx
+//     (the MUFU unit, 32 results/clk/SM on GB300) and accumulate e * p_j into
+//     block I's row sums and e * p_i into block J's column sums with packed
+//     float32x2 FMAs, overlapping the tensor-core work of the next tiles.
+// Row sums go to a per-segment partial buffer and column sums to a per-tile
+// one; a finishing kernel adds lambda p, sums a row's partials in a fixed
+// order and performs the PCG p^T w reduction.
 // Every mbarrier wait is bounded; on timeout the kernel raises an error word,
 // drains its own copies, frees its tensor memory and returns.
 #include <cuda.h>

@@ -1,16 +1,18 @@
 // Preconditioned conjugate gradient on GB300 (Sec. IV-E, Algorithm 1, PCG stage).
 //
-// One PCG iteration is four kernels, all reading their scalars from device
-// memory so that a block of iterations is captured once into a CUDA graph and
-// replayed; the host only polls a convergence word between replays:
+// One PCG iteration is a fixed sequence of kernels, all reading their scalars
+// from device memory so that a block of iterations is captured once into a
+// CUDA graph and replayed; the host only polls a convergence word between
+// replays:
 //
 //   MV   p = z + beta p_old (fused prologue), w = (lambda I + G) p,
-//        p^T w  -> last block: delta = r.z / p^T A p          (HBM-bound stream of G)
-//   UPD  alpha += delta p, r -= delta w, |r|^2, U^T r partials
-//        -> last block: stop test, t = U^T r
+//        p^T w  -> last block: delta = r.z / p^T A p
+//        (materialised: a stream of G; matrix-free: prep, tcgen05 kernel, finish)
+//   UPD  alpha += delta p, r -= delta w, |r|^2 -> last block: stop test
 //   [TR1, TR2]  only when a float64-accurate residual is due (mixed forms):
 //        w2 = (lambda I + G) alpha in compensated double-float, r = y - w2
 //        replaces the recursive residual (reliable updates), stop test on |r|
+//   UTR  t = U^T r as partial sums over row chunks (CCCP preconditioner)
 //   PRE  z = P r, r^T z -> last block: beta = r.z_new / r.z_old
 //
 // The replaced residual must be accurate well below the tolerance: near
