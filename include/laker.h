@@ -173,6 +173,45 @@ laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_pre
                              const double* y, double* alpha, double tol, int max_iter,
                              int refine_every, laker_solve_info* info);
 
+/*
+ * laker_pcg_solve that also records, for every product k = 1 .. min(iterations,
+ * trace_cap), four float64 values in trace[4 (k-1) ..] (host memory, owned by
+ * the caller; rows past the last product are zeroed):
+ *   delta_k          the step of product k;
+ *   |r_k|^2 / |y|^2  the recursive residual after it;
+ *   R(alpha_k)       |G alpha - y|^2 + lambda alpha^T G alpha (Eq. simu-R-definition),
+ *                    from the recursive residual: |r|^2 + lambda (r.alpha + y.alpha);
+ *   beta_k           the conjugation coefficient formed after it (0 past the last).
+ * These feed the paper's numerical-layer metrics (Sec. V-A): iterations to an
+ * objective gap (laker_trace_gap_iterations) and the condition-number
+ * estimate from the Lanczos tridiagonal (laker_lanczos_extremes).  For mixed
+ * solves the values follow the recursive residual between replacements.
+ * Errors: as laker_pcg_solve; LAKER_ERR_ARG for trace_cap < 1 or trace NULL.
+ */
+laker_status laker_pcg_solve_trace(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
+                                   const double* y, double* alpha, double tol, int max_iter,
+                                   int refine_every, laker_solve_info* info, double* trace, int trace_cap);
+
+/*
+ * Extreme eigenvalues of the Lanczos tridiagonal T_k of k PCG products (host
+ * arithmetic on a trace of laker_pcg_solve_trace): T_jj = 1/delta_j +
+ * beta_{j-1}/delta_{j-1}, T_j,j+1 = sqrt(beta_j)/delta_j.  Its eigenvalues are
+ * the Ritz values of P^1/2 (lambda I + G) P^1/2 on the Krylov space, so
+ * lmax / lmin estimates kappa(P (lambda I + G)) from below (Sec. V-A, the
+ * condition-number metric), exactly once k reaches the number of distinct
+ * eigenvalues.  Bisection on Sturm counts, relative accuracy ~1e-14.
+ * Errors: LAKER_ERR_ARG for k < 1, NULL pointers, delta <= 0 or beta < 0.
+ */
+laker_status laker_lanczos_extremes(const double* trace, int k, double* lmin, double* lmax);
+
+/*
+ * The first product k (1-based) of a trace whose objective gap
+ * |R(alpha_k) - R_ref| / |R_ref| is <= gap (Eq. iterations with TAR.TOL =
+ * gap; R_ref from a reference solution), or -1 if none of the k_max rows
+ * reaches it.
+ */
+int laker_trace_gap_iterations(const double* trace, int k_max, double R_ref, double gap);
+
 /* One instance of a batched solve: its operator, preconditioner (NULL =
  * identity), right-hand side y (device, n) and output alpha (device, n). */
 typedef struct {

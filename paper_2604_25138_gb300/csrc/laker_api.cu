@@ -1,7 +1,9 @@
 // C ABI of liblaker: argument checks, handle lifetime, dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "laker_internal.h"
 
@@ -316,6 +318,72 @@ laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_pre
     if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
     if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
     return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info);
+}
+
+laker_status laker_pcg_solve_trace(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
+                                   double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info,
+                                   double* trace, int trace_cap) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !y || !alpha || !trace) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (trace_cap < 1) return set_error(ctx, LAKER_ERR_ARG, "need trace_cap >= 1");
+    if (!(tol >= 0.0) || max_iter < 1 || refine_every < 0) return set_error(ctx, LAKER_ERR_ARG, "bad PCG parameters");
+    if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
+    if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
+    return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info, trace, trace_cap);
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (a, b) below x: the
+// negative pivots of the LDL^T factorisation of T - x I (Sturm count).
+static int sturm_below(const std::vector<double>& a, const std::vector<double>& b, double x) {
+    int count = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        q = (a[i] - x) - (i > 0 ? b[i - 1] * b[i - 1] / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++count;
+    }
+    return count;
+}
+
+laker_status laker_lanczos_extremes(const double* trace, int k, double* lmin, double* lmax) {
+    if (!trace || !lmin || !lmax || k < 1) return LAKER_ERR_ARG;
+    std::vector<double> a((size_t)k), b((size_t)std::max(0, k - 1));
+    for (int j = 0; j < k; ++j) {
+        const double d = trace[4 * j], bp = (j > 0) ? trace[4 * (j - 1) + 3] : 0.0, dp = (j > 0) ? trace[4 * (j - 1)] : 1.0;
+        if (!(d > 0.0) || !(bp >= 0.0)) return LAKER_ERR_ARG;
+        a[(size_t)j] = 1.0 / d + bp / dp;
+        if (j + 1 < k) {
+            const double bj = trace[4 * j + 3];
+            if (!(bj >= 0.0)) return LAKER_ERR_ARG;
+            b[(size_t)j] = std::sqrt(bj) / d;
+        }
+    }
+    double lo = a[0], hi = a[0];
+    for (int j = 0; j < k; ++j) {   // Gershgorin interval
+        const double r = (j > 0 ? std::fabs(b[(size_t)j - 1]) : 0.0) + (j + 1 < k ? std::fabs(b[(size_t)j]) : 0.0);
+        lo = std::min(lo, a[(size_t)j] - r);
+        hi = std::max(hi, a[(size_t)j] + r);
+    }
+    auto kth = [&](int idx) {   // idx-th smallest eigenvalue by bisection
+        double l = lo, h = hi;
+        for (int it = 0; it < 400 && h - l > 1e-15 * std::max(std::fabs(l), std::fabs(h)); ++it) {
+            const double mid = 0.5 * (l + h);
+            if (sturm_below(a, b, mid) > idx) h = mid;
+            else l = mid;
+        }
+        return 0.5 * (l + h);
+    };
+    *lmin = kth(0);
+    *lmax = kth(k - 1);
+    return LAKER_OK;
+}
+
+int laker_trace_gap_iterations(const double* trace, int k_max, double R_ref, double gap) {
+    if (!trace || k_max < 1 || !(R_ref != 0.0)) return -1;
+    for (int k = 0; k < k_max; ++k)
+        if (std::fabs(trace[4 * k + 2] - R_ref) <= gap * std::fabs(R_ref)) return k + 1;
+    return -1;
 }
 
 laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items, double tol,

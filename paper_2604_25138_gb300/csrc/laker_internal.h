@@ -27,6 +27,9 @@ struct PcgScalars {
     int refine_every;   // 0 = never replace the residual
     int pad0, pad1;
     unsigned int ticket[8];
+    double* trace;      // per product k: delta, |r|^2/|y|^2, R(alpha), beta (4 doubles), or null
+    int trace_cap;      // products the trace holds
+    int pad2;
 };
 
 struct laker_ctx {
@@ -115,7 +118,8 @@ laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x,
 // laker_pcg.cu
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
                        const double* y, double* alpha, double tol, int max_iter,
-                       int refine_every, laker_solve_info* info);
+                       int refine_every, laker_solve_info* info, double* trace = nullptr,
+                       int trace_cap = 0);
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
 // laker_fit.cu
 void release_cublas(laker_ctx* ctx);

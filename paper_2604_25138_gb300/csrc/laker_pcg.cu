@@ -22,6 +22,7 @@
 //
 // All cross-block sums go through per-block partials reduced in a fixed order
 // by the last block to finish (atomic ticket), so results are deterministic.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -290,26 +291,53 @@ k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, 
 // UPD: alpha += delta p, r -= delta w, |r|^2; stop / refinement decisions.
 __global__ void __launch_bounds__(VEC_THREADS)
 k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ alpha,
-             double* __restrict__ r, PcgScalars* sc, double* __restrict__ partials) {
+             double* __restrict__ r, PcgScalars* sc, double* __restrict__ partials, const double* __restrict__ y,
+             double lambda) {
     if (gated_out(sc, GATE_RUNNING)) return;
     __shared__ double red[VEC_THREADS / 32];
     int64_t r0, r1;
     row_range(n, r0, r1);
     const double delta = sc->delta;
-    double rr = 0.0;
+    double* trace = sc->trace;   // uniform: the trace also needs r.alpha and y.alpha
+    double rr = 0.0, ra = 0.0, ya = 0.0;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        alpha[i] = fma(delta, p[i], alpha[i]);
+        const double ai = fma(delta, p[i], alpha[i]);
+        alpha[i] = ai;
         const double ri = fma(-delta, w[i], r[i]);
         r[i] = ri;
         rr = fma(ri, ri, rr);
+        if (trace) {
+            ra = fma(ri, ai, ra);
+            ya = fma(y[i], ai, ya);
+        }
     }
     rr = lk::block_sum(rr, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = rr;
+    if (trace) {
+        ra = lk::block_sum(ra, red);
+        ya = lk::block_sum(ya, red);
+        if (threadIdx.x == 0) {
+            partials[gridDim.x + blockIdx.x] = ra;
+            partials[2 * gridDim.x + blockIdx.x] = ya;
+        }
+    }
     if (lk::last_block(&sc->ticket[2])) {
         const double tot = lk::sum_partials(partials, gridDim.x, red);
+        double tra = 0.0, tya = 0.0;
+        if (trace) {
+            tra = lk::sum_partials(partials + gridDim.x, gridDim.x, red);
+            tya = lk::sum_partials(partials + 2 * gridDim.x, gridDim.x, red);
+        }
         if (threadIdx.x == 0) {
             sc->rr = tot;
             const int it = sc->iters;
+            // R(alpha) = |G alpha - y|^2 + lambda alpha^T G alpha with G alpha = y - r - lambda alpha
+            // (Eq. simu-R-definition) is |r|^2 + lambda (r.alpha + y.alpha)
+            if (trace && it >= 1 && it <= sc->trace_cap) {
+                trace[4 * (it - 1)] = delta;
+                trace[4 * (it - 1) + 1] = tot / sc->yy;
+                trace[4 * (it - 1) + 2] = fma(lambda, tra + tya, tot);
+            }
             const bool small = tot <= sc->tol2yy;
             if (!isfinite(tot)) {
                 sc->converged = 2;
@@ -554,6 +582,8 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
             else if (tot == 0.0) sc->converged = 1;
             sc->beta = (old > 0.0) ? tot / old : 0.0;
             sc->rz = tot;
+            const int it = sc->iters;
+            if (sc->trace && it >= 1 && it <= sc->trace_cap) sc->trace[4 * (it - 1) + 3] = sc->beta;
             sc->ticket[4] = 0;
         }
     }
@@ -728,7 +758,8 @@ laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecVie
                               ws.mv_blocks);
     }
     if (st != LAKER_OK) return st;
-    k_pcg_update<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, pout, ws.w, alpha, ws.r, ws.sc, ws.partials);
+    k_pcg_update<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, pout, ws.w, alpha, ws.r, ws.sc, ws.partials, y,
+                                                                  op->lambda);
     LK_LAUNCHED(ctx);
     if (mixed) {
         // TR1: w2 = (lambda I + G) alpha in double-float, only when a true residual is due
@@ -832,7 +863,8 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
 }
 
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
-                       double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info) {
+                       double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info,
+                       double* trace, int trace_cap) {
     const int64_t n = op->n;
     const bool mixed = (op->precision != LAKER_FP64) && refine_every > 0;
     const bool use32 = (op->precision != LAKER_FP64);
@@ -848,6 +880,20 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     PcgScalars init{};
     init.max_iter = max_iter;
     init.refine_every = mixed ? refine_every : 0;
+    struct TraceBuf {
+        double* p = nullptr;
+        ~TraceBuf() { cudaFree(p); }
+    } tb;
+    double*& dtrace = tb.p;
+    if (trace && trace_cap > 0) {
+        if ((st = lk_malloc(ctx, (void**)&dtrace, (size_t)4 * trace_cap * sizeof(double))) != LAKER_OK) {
+            ws_free(ws);
+            return st;
+        }
+        LK_CUDA(ctx, cudaMemsetAsync(dtrace, 0, (size_t)4 * trace_cap * sizeof(double), ctx->stream));
+        init.trace = dtrace;
+        init.trace_cap = trace_cap;
+    }
     LK_CUDA(ctx, cudaMemcpyAsync(ws.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
 
     auto run_init = [&]() -> laker_status {
@@ -911,6 +957,14 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     LK_CUDA(ctx, cudaMemcpyAsync(&out, ws.sc, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
     LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ws_free(ws);
+    if (dtrace) {
+        const int rows = std::min(out.iters, trace_cap);
+        for (int i = rows; i < trace_cap; ++i)
+            for (int q = 0; q < 4; ++q) trace[4 * i + q] = 0.0;
+        cudaError_t ce2 = rows > 0 ? cudaMemcpy(trace, dtrace, (size_t)4 * rows * sizeof(double), cudaMemcpyDeviceToHost)
+                                   : cudaSuccess;
+        if (ce2 != cudaSuccess) return set_error(ctx, LAKER_ERR_CUDA, std::string("trace copy: ") + cudaGetErrorString(ce2));
+    }
     laker_status result = LAKER_OK;
     if (out.converged == 2) result = LAKER_ERR_BREAKDOWN;
     else if (out.converged != 1) result = LAKER_ERR_MAXITER;

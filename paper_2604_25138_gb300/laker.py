@@ -93,6 +93,10 @@ def library() -> ctypes.CDLL:
         "laker_precond_apply": (i32, [vp, vp, vp, vp]),
         "laker_precond_export": (i32, [vp, vp, vp, vp, vp]),
         "laker_pcg_solve": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
+        "laker_pcg_solve_trace": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo),
+                                        ctypes.POINTER(f64), i32]),
+        "laker_lanczos_extremes": (i32, [ctypes.POINTER(f64), i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]),
+        "laker_trace_gap_iterations": (i32, [ctypes.POINTER(f64), i32, f64, f64]),
         "laker_eval_map": (i32, [vp, vp, vp, i64, vp, vp]),
         "laker_eval_map_method": (i32, [vp, vp, vp, i64, vp, vp, i32]),
         "laker_eval_map_noalloc": (i32, [vp, vp, vp, i64, vp, vp]),
@@ -410,6 +414,49 @@ def laker_pcg_solve(ctx: Context, op: Operator, P: Preconditioner | None, y: tor
                                        ctypes.byref(info))
     ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
     return alpha, {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+
+def laker_pcg_solve_trace(ctx: Context, op: Operator, P: Preconditioner | None, y: torch.Tensor, tol: float,
+                          max_iter: int = 100000, refine_every: int = 0, alpha: torch.Tensor | None = None,
+                          allow_maxiter: bool = False, trace_cap: int | None = None):
+    """laker_pcg_solve that also returns the per-product trace as a
+    (products x 4) float64 array: delta, |r|^2/|y|^2, R(alpha), beta."""
+    import numpy as np
+    if alpha is None:
+        alpha = torch.empty_like(y)
+    cap = int(trace_cap if trace_cap is not None else max_iter)
+    trace = np.zeros(4 * cap, dtype=np.float64)
+    info = SolveInfo()
+    with ctx:
+        st = library().laker_pcg_solve_trace(ctx.handle, op.handle, P.handle if P is not None else None,
+                                             _ptr(y, "y", op.n), _ptr(alpha, "alpha", op.n), tol, max_iter,
+                                             refine_every, ctypes.byref(info),
+                                             trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap)
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    d = {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+    rows = min(d["iterations"], cap)
+    return alpha, d, trace.reshape(cap, 4)[:rows].copy()
+
+
+def laker_lanczos_extremes(trace, k: int | None = None):
+    """(lmin, lmax) of the Lanczos tridiagonal of the first k rows of a trace."""
+    import numpy as np
+    t = np.ascontiguousarray(trace, dtype=np.float64)
+    k = int(t.shape[0] if k is None else k)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    st = library().laker_lanczos_extremes(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), k, ctypes.byref(lo),
+                                          ctypes.byref(hi))
+    if st != OK:
+        raise LakerError(st, "laker_lanczos_extremes: bad trace")
+    return lo.value, hi.value
+
+
+def laker_trace_gap_iterations(trace, R_ref: float, gap: float = 1e-3) -> int:
+    """First product (1-based) whose objective gap to R_ref is <= gap, or -1."""
+    import numpy as np
+    t = np.ascontiguousarray(trace, dtype=np.float64)
+    return int(library().laker_trace_gap_iterations(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), t.shape[0],
+                                                    float(R_ref), float(gap)))
 
 
 def laker_pcg_solve_batched(ctx: Context, items, tol: float, max_iter: int = 100000, refine_every: int = 0,
