@@ -139,8 +139,14 @@ laker_status laker_op_time_operator(laker_ctx* ctx, const laker_op* op, const do
  *   rho     < 0 selects the adaptive rule min(1/2, max(1e-3, gamma (1 - n_r/n)))
  *           (1e-3 when n_r >= n).
  *   eps     safeguard of F_gamma (> 0).
+ * Precision: float64 throughout for FP64 operators.  For FP32 and BF16X3
+ * operators the products G z_k use the materialised float32 G through cuBLAS
+ * (bf16x9 float32 emulation on the tensor cores; a cuBLAS handle is created
+ * on the context's first fit and released by laker_destroy), and P is kept in
+ * the orthonormal form c^-1/2 I + U~ diag(phi) U~^T over the eigen-directions
+ * of D^1/2 M D^1/2 with eigenvalue > 1e-3 c (float32 U~).
  * Errors: LAKER_ERR_ARG for n_r < 1 or n_r > 2048; LAKER_ERR_NOT_SPD if a
- * factorisation fails.
+ * factorisation fails; LAKER_ERR_CUDA if cuBLAS fails.
  */
 laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z,
                                       int n_r, double gamma, double rho, double eps,
