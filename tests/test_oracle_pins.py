@@ -382,3 +382,107 @@ def test_shrinkage_rule_reading():
     vals = [O.shrinkage_rho(1000, m, 0.1) for m in (900, 500, 100, 10)]
     assert all(a <= b for a, b in zip(vals, vals[1:]))
     assert O.shrinkage_rho(1000, 10, 5.0) == 0.5
+
+
+# --------------------------------------------------------------------------
+# Metrics with hand-worked values (Sec. V-A, Eqs. objective-gap and
+# prediction-discrepancy), the Jacobi baseline and the condition number
+# --------------------------------------------------------------------------
+
+def _R_exact(G, a, y, lam):
+    """R(alpha) = |G alpha - y|^2 + lambda alpha^T G alpha in exact rationals,
+    written as explicit loops over the entries."""
+    n = len(y)
+    Ga = [sum((G[i][j] * a[j] for j in range(n)), Fraction(0)) for i in range(n)]
+    fit = sum(((Ga[i] - y[i]) ** 2 for i in range(n)), Fraction(0))
+    reg = sum((a[i] * Ga[i] for i in range(n)), Fraction(0))
+    return fit + lam * reg
+
+
+def test_objective_gap_and_prediction_discrepancy_hand_worked_2x2():
+    """G = [[2, 1], [1, 3]], y = (1, 2), lambda = 1/2, alpha = (1, 0),
+    alpha_ref = (0, 1).  By hand: G alpha = (2, 1), |G alpha - y|^2 = 2,
+    alpha^T G alpha = 2, so R(alpha) = 3; G alpha_ref = (1, 3),
+    |G alpha_ref - y|^2 = 1, alpha_ref^T G alpha_ref = 3, so R(alpha_ref) = 5/2.
+    Objective gap |3 - 5/2| / (5/2) = 1/5.  Prediction discrepancy
+    |(2, 1) - (1, 3)| / |(1, 3)| = sqrt(5) / sqrt(10) = 1/sqrt(2).
+    A dropped lambda term (gap 1), lambda alpha^T alpha in place of
+    alpha^T G alpha (gap 2/3), normalising by R(alpha) (1/6), or comparing
+    alpha instead of G alpha (sqrt 2) all fail."""
+    G = np.array([[2.0, 1.0], [1.0, 3.0]])
+    y = np.array([1.0, 2.0])
+    a = np.array([1.0, 0.0])
+    a_ref = np.array([0.0, 1.0])
+    assert O.objective_R(G, a, y, 0.5) == 3.0
+    assert O.objective_R(G, a_ref, y, 0.5) == 2.5
+    assert abs(O.objective_gap(G, a, a_ref, y, 0.5) - 0.2) < 1e-15
+    assert abs(O.prediction_discrepancy(G, a, a_ref) - 1.0 / math.sqrt(2.0)) < 1e-15
+
+
+def test_objective_gap_and_prediction_discrepancy_exact_3x3():
+    """A non-symmetric-looking but symmetric 3 x 3 G with rational entries,
+    unequal alpha and alpha_ref: the oracle's float64 metrics against exact
+    rational arithmetic (squared discrepancy compared, to stay rational)."""
+    Gq = [[Fraction(5, 2), Fraction(1, 3), Fraction(-1, 4)],
+          [Fraction(1, 3), Fraction(7, 5), Fraction(1, 6)],
+          [Fraction(-1, 4), Fraction(1, 6), Fraction(9, 8)]]
+    yq = [Fraction(3, 2), Fraction(-1, 2), Fraction(2, 7)]
+    aq = [Fraction(1, 5), Fraction(-3, 4), Fraction(5, 3)]
+    rq = [Fraction(-2, 3), Fraction(1, 2), Fraction(1, 9)]
+    lam = Fraction(3, 10)
+    G = np.array([[float(v) for v in row] for row in Gq])
+    y, a, r = (np.array([float(v) for v in vec]) for vec in (yq, aq, rq))
+    R_a, R_r = _R_exact(Gq, aq, yq, lam), _R_exact(Gq, rq, yq, lam)
+    gap = abs(R_a - R_r) / abs(R_r)
+    assert abs(O.objective_gap(G, a, r, y, float(lam)) - float(gap)) < 1e-14 * float(gap)
+    Ga = [sum(Gq[i][j] * aq[j] for j in range(3)) for i in range(3)]
+    Gr = [sum(Gq[i][j] * rq[j] for j in range(3)) for i in range(3)]
+    disc2 = sum((Ga[i] - Gr[i]) ** 2 for i in range(3)) / sum(v * v for v in Gr)
+    pd = O.prediction_discrepancy(G, a, r)
+    assert abs(pd * pd - float(disc2)) < 1e-14 * float(disc2)
+
+
+def test_jacobi_preconditioner_is_the_inverse_diagonal():
+    """P_J = diag(A)^-1 (Sec. V-A baseline).  On a diagonal A with distinct
+    entries P_J is A^-1 exactly, so P_J A = I and PCG stops after one product;
+    on a full SPD A, P_J is diagonal and P_J A has a unit diagonal.  diag(A)
+    in place of its inverse, diag(A)^-1/2, or the full inverse all fail."""
+    a = np.array([0.5, 2.0, 8.0, 32.0, 0.125])          # exact binary fractions
+    A = np.diag(a)
+    PJ = O.jacobi_preconditioner(A)
+    assert np.array_equal(PJ @ A, np.eye(5))
+    res = O.pcg(A, np.array([1.0, -2.0, 3.0, 0.5, 4.0]), PJ, 1e-14)
+    assert res.converged and res.iterations == 1
+    inst = synth.make_instance(60, 8, 1e-2, seed=19, grid=2)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    PJ = O.jacobi_preconditioner(A)
+    assert np.array_equal(PJ, np.diag(np.diag(PJ)))
+    np.testing.assert_allclose(np.diag(PJ @ A), np.ones(60), rtol=2e-16, atol=0)
+
+
+def test_condition_number_of_a_known_spectrum():
+    """A = V diag(a) V^T and P = V diag(p) V^T share eigenvectors, so the
+    eigenvalues of P A are a_k p_k and kappa(P A) = max(a p) / min(a p)
+    exactly; for a P that does not commute with A, kappa(P A) equals the
+    ratio of the extreme generalised eigenvalues of A x = mu P^-1 x."""
+    rng = np.random.default_rng(23)
+    V, _ = np.linalg.qr(rng.normal(size=(12, 12)))
+    a = np.geomspace(1e-3, 1e3, 12)
+    p = np.geomspace(5.0, 0.02, 12)
+    A = (V * a) @ V.T
+    A = 0.5 * (A + A.T)
+    P = (V * p) @ V.T
+    P = 0.5 * (P + P.T)
+    want = float(np.max(a * p) / np.min(a * p))
+    assert abs(O.condition_number(A, P) - want) < 1e-8 * want
+    assert abs(O.condition_number(A) - 1e6) < 1e-6 * 1e6
+    W, _ = np.linalg.qr(rng.normal(size=(12, 12)))
+    P2 = (W * np.geomspace(0.1, 10.0, 12)) @ W.T
+    P2 = 0.5 * (P2 + P2.T)
+    mu = scipy_eigh_general(A, np.linalg.inv(P2))
+    assert abs(O.condition_number(A, P2) - mu[-1] / mu[0]) < 1e-7 * (mu[-1] / mu[0])
+
+
+def scipy_eigh_general(A, B):
+    import scipy.linalg
+    return scipy.linalg.eigh(A, 0.5 * (B + B.T), eigvals_only=True)
