@@ -1,16 +1,20 @@
-"""Benchmark: PCG solves/s at a true relative residual of 1e-6 on one large
-radio-map instance (n = 16384 clustered locations, d = 32, lambda = 1e-4,
-8 transmitters, 512 x 512 query grid).
+"""Benchmark: PCG solves/s at a true relative residual of 1e-6, mixed
+precision against plain float64, on the precision-form instance (n = 65536
+uniform locations in a 1 km square, d = 64, lambda = 1e-4, 8 transmitters,
+N_r = 2048 random directions, 512 x 512 query grid).
 
 One step = the whole hot path on one instance: kernel construction, CCCP
-preconditioner fit (N_r random directions), mixed-precision PCG with a
-float64-accurate residual every 20 products, radio-map evaluation.  Inputs are
-resident in HBM when the timed region starts (`value`); `e2e` repeats the
-step through the same public API with pinned host buffers copied in and the
-results copied out inside the timed region.  The plain float64 path (the
-paper's method run in float64 throughout) is timed beside it.
+preconditioner fit, mixed-precision PCG (split-bf16 tensor-core operator,
+float64 scalars, float64-accurate residual every 20 products) to the true
+tolerance, radio-map evaluation.  Inputs are resident in HBM when the timed
+region starts (`value`); `e2e` repeats the step through the same public API
+with pinned host buffers copied in and the results copied out inside the timed
+region.  The plain float64 path (the paper's method run in float64
+throughout) is timed on the same instance in the same run, and the line
+reports the mixed alpha's error against it and the dB RMSE of the two maps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c3|c2|batched|learned|sweep]
 
 Multi-GPU: the instance does not shard; N ranks run N independent replicas
 (different seeds), `value` = instances solved by all ranks / max rank time.
@@ -34,23 +38,33 @@ sys.path.insert(0, ROOT)
 
 from paper_2604_25138_gb300 import synth  # noqa: E402
 
-METRIC = "PCG solves/s at rel-res 1e-6 (mixed)"
+METRIC = "PCG solves/s at rel-res 1e-6 (mixed, vs plain FP64)"
 UNIT = "solves/s"
-CFG = dict(n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6, refine_every=20)
-SEED = 2000
-# DRAM bytes (read + write) of one k_mf_bf16x3 launch at this workload, from the
-# ncu capture summarised in profiles/k_mf_bf16x3_n16384_d32.md (None until a
-# capture of the current kernel exists); the operands Q_hi, Q_lo are read from
-# DRAM once, everything else stays in L2.
-MF_TRAFFIC_BYTES = 2205696
+# single-instance workloads: the precision form (headline) and the larger
+# plain-method instance
+SINGLE = {
+    "c3": dict(name="precision form: single instance, n=65536 uniform, d=64, lambda=1e-4, 8 Tx, 512x512 grid",
+               n=65536, d=64, lam=1e-4, n_tx=8, layout="uniform", grid=512, tol=1e-6, refine_every=20, seed=3000),
+    "c2": dict(name="single instance, n=16384 (70% uniform, 30% in 5 blobs), d=32, lambda=1e-4, 8 Tx, 512x512 grid",
+               n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6, refine_every=20, seed=2000),
+}
+# the bounded oracle sample timed on the host cores: the same generator as the
+# workload at n = 2048 (the dense oracle's CCCP costs O(n^3) per iteration:
+# ~12 s at n = 2048, ~50 s at n = 4096 and ~5 min at n = 8192 on 8 cores)
+CPU_SAMPLE_N = 2048
+CPU_SAMPLE_GRID = 64
+# DRAM bytes (read + write) of one k_mf_bf16x3 launch from an ncu capture of
+# the current kernel at the workload's size, or None
+MF_TRAFFIC_BYTES = None
+SFU_EX2_PER_CLK_PER_SM = 32   # ex2.approx results per clock per SM (micro-benchmarked on GB300)
 
 
-def workload(seed: int):
-    c = CFG
-    inst = synth.make_instance(c["n"], c["d"], c["lam"], n_tx=c["n_tx"], seed=seed, layout=c["layout"],
-                               grid=c["grid"])
-    n_r = synth.default_num_directions(c["n"])
-    Z = synth.directions(c["n"], n_r, seed)
+def workload(cfg: dict, seed: int, n: int | None = None, grid: int | None = None):
+    n = cfg["n"] if n is None else n
+    inst = synth.make_instance(n, cfg["d"], cfg["lam"], n_tx=cfg["n_tx"], seed=seed, layout=cfg["layout"],
+                               grid=cfg["grid"] if grid is None else grid)
+    n_r = synth.default_num_directions(n)
+    Z = synth.directions(n, n_r, seed)
     return inst, Z, n_r
 
 
@@ -139,6 +153,7 @@ def run_ours(args):
     from paper_2604_25138_gb300 import build
     from paper_2604_25138_gb300 import laker as L
 
+    cfg = SINGLE[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -147,8 +162,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     dev_t = torch.device("cuda", local)
-    inst, Zh, n_r = workload(SEED + rank)
-    c = CFG
+    inst, Zh, n_r = workload(cfg, cfg["seed"] + rank)
+    n = inst.n
 
     def to_dev(x):
         return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev_t)
@@ -156,32 +171,48 @@ def run_ours(args):
     Q, y, Z, Qg = to_dev(inst.Q), to_dev(inst.y), to_dev(Zh), to_dev(inst.Qg)
     ctx = L.Context(local)
 
-    def step(Q, y, Z, Qg, precision, refine):
-        op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, precision)
-        P = L.laker_fit_preconditioner(ctx, op, Z)
-        alpha, info = L.laker_pcg_solve(ctx, op, P, y, c["tol"], max_iter=20000, refine_every=refine)
-        fmap = L.laker_eval_map(ctx, op, Qg, alpha)
-        P.close()
-        op.close()
-        return alpha, fmap, info, P.info
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(ctx.stream)
+        return e
 
-    mixed = dict(precision=L.BF16X3, refine=c["refine_every"])
+    def step(Q, y, Z, Qg, precision, refine, tol, keep=False, phases=None):
+        e0 = ev()
+        op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, precision)
+        e1 = ev()
+        P = L.laker_fit_preconditioner(ctx, op, Z)
+        e2 = ev()
+        alpha, info = L.laker_pcg_solve(ctx, op, P, y, tol, max_iter=40000, refine_every=refine)
+        e3 = ev()
+        fmap = L.laker_eval_map(ctx, op, Qg, alpha)
+        e4 = ev()
+        if phases is not None:
+            e4.synchronize()
+            phases.append({"build": e0.elapsed_time(e1), "fit": e1.elapsed_time(e2), "solve": e2.elapsed_time(e3),
+                           "map": e3.elapsed_time(e4)})
+        P.close()
+        if not keep:
+            op.close()
+            op = None
+        return alpha, fmap, info, P.info, op
+
+    mixed = dict(precision=L.BF16X3, refine=cfg["refine_every"], tol=cfg["tol"])
     for _ in range(args.warmup):
         step(Q, y, Z, Qg, **mixed)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = ctx.launches()
+    phases = []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
-        ev0.record(ctx.stream)
+        ev0 = ev()
         t0 = time.perf_counter()
         infos = []
         for _ in range(args.steps):
-            alpha, fmap, info, finfo = step(Q, y, Z, Qg, **mixed)
+            alpha, fmap, info, finfo, _ = step(Q, y, Z, Qg, phases=phases, **mixed)
             infos.append((info, finfo))
-        ev1.record(ctx.stream)
+        ev1 = ev()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     launches = ctx.launches() - launches0
@@ -194,46 +225,49 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     info, finfo = infos[-1]
+    alpha_m, fmap_m = alpha.clone(), fmap.clone()
 
     # end to end through the public API with pinned host buffers
     hosts = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (inst.Q, inst.y, Zh, inst.Qg)]
     h2d = sum(h.numel() * 8 for h in hosts)
-    out_a = torch.empty(inst.n, dtype=torch.float64).pin_memory()
+    out_a = torch.empty(n, dtype=torch.float64).pin_memory()
     out_m = torch.empty(inst.Qg.shape[0], dtype=torch.float64).pin_memory()
     d2h = (out_a.numel() + out_m.numel()) * 8
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 2))
     for _ in range(e2e_steps):
         dQ, dy, dZ, dQg = (h.to(dev_t, non_blocking=True) for h in hosts)
-        a, fm, _, _ = step(dQ, dy, dZ, dQg, **mixed)
+        a, fm, _, _, _ = step(dQ, dy, dZ, dQg, **mixed)
         out_a.copy_(a, non_blocking=True)
         out_m.copy_(fm, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    # roofline of the dominant kernel: the tcgen05 matrix-free operator.  It
-    # computes each unordered pair of points once (n(n+1)/2 pairs, as 128 x 128
-    # tiles of the block pairs I <= J): per pair 4 split-bf16 products of
-    # 2 * dpad flops on the tensor pipe and one ex2 on the MUFU pipe; the
-    # binding roof is the larger of the two times.
+    # roofline of the dominant kernel: the matrix-free product.  The method's
+    # own work per unique pair (n(n+1)/2 pairs; the operator is symmetric) is
+    # the three split-bf16 products hi.hi + hi.lo + lo.hi of 2 d flops each on
+    # the tensor pipe and one ex2 on the MUFU pipe; the roof is the larger of
+    # the two times.  The kernel's fourth product (lo.lo) and the padding of
+    # the tiles are implementation work and are not counted.  The time is that
+    # of the whole product as PCG issues it (preparation, tensor-core kernel,
+    # finish).
     op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.BF16X3)
-    x = to_dev(synth.random_vector(inst.n, 1))
-    mv_ms = L.laker_op_time_operator(ctx, op, x, reps=30)
+    x = to_dev(synth.random_vector(n, 1))
+    prod_ms = L.laker_op_time_product(ctx, op, x, reps=20)
+    main_ms = L.laker_op_time_operator(ctx, op, x, reps=20)
     op.close()
-    n = inst.n
-    dpad = (inst.d + 15) // 16 * 16
-    nb = (n + 127) // 128
-    pairs = float(nb * (nb + 1) // 2) * 128 * 128
-    flops = pairs * 4 * 2 * dpad
+    pairs = n * (n + 1) / 2.0
+    flops = pairs * 3 * 2 * inst.d
     bf16_peak, peak_kind = peaks_bf16()
-    sfu_peak = 32 * 152 * 2.07e9                     # ex2/s: 32 per clock per SM (measured) x SMs x max clock
+    sfu_peak = SFU_EX2_PER_CLK_PER_SM * 152 * 2.07e9
     t_tensor = flops / (bf16_peak * 1e12)
     t_sfu = pairs / sfu_peak
-    achieved = flops / (mv_ms * 1e-3) / 1e12
-    # the streamed float32 materialised matvec, for the variant comparison
+    achieved = flops / (prod_ms * 1e-3) / 1e12
+    bound = "tensor" if t_tensor >= t_sfu else "sfu"
+    # the streamed float32 materialised product, for the variant choice per n
     opm = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32)
-    mat_ms = L.laker_op_time_operator(ctx, opm, x, reps=30)
+    mat_ms = L.laker_op_time_product(ctx, opm, x, reps=10)
     opm.close()
     ldk = (n + 3) // 4 * 4
     mat_gbs = (n * ldk * 4 + 3 * n * 8) / (mat_ms * 1e-3) / 1e9
@@ -241,15 +275,28 @@ def run_ours(args):
 
     # plain float64 path on the same instance (the paper's method in float64)
     plain = None
+    accuracy = None
     if args.plain_steps > 0:
         torch.cuda.synchronize()
         p0 = time.perf_counter()
-        for _ in range(args.plain_steps):
-            _, _, pinfo, _ = step(Q, y, Z, Qg, precision=L.FP64, refine=0)
+        for k in range(args.plain_steps):
+            a64, f64, pinfo, pfinfo, op64 = step(Q, y, Z, Qg, precision=L.FP64, refine=0, tol=cfg["tol"],
+                                                  keep=(k == args.plain_steps - 1))
         torch.cuda.synchronize()
         pm = (time.perf_counter() - p0) * 1e3 / args.plain_steps
         plain = {"solves_per_s": 1e3 / pm, "ms_per_step": pm, "iterations": pinfo["iterations"],
-                 "rel_res_true": pinfo["rel_res_true"]}
+                 "cccp_iterations": pfinfo["iterations"], "rel_res_true": pinfo["rel_res_true"]}
+        # accuracy of the mixed run against the float64 run: alpha, the map in
+        # dB over the whole grid, and the mixed alpha's true residual by the
+        # float64 operator
+        w = L.laker_op_matvec(ctx, op64, alpha_m)
+        res_m = float(torch.linalg.norm(y - w) / torch.linalg.norm(y))
+        op64.close()
+        accuracy = {"alpha_rel_err": float(torch.linalg.norm(alpha_m - a64) / torch.linalg.norm(a64)),
+                    "map_db_rmse": float(inst.y_sigma * torch.sqrt(torch.mean((fmap_m - f64) ** 2))),
+                    "map_db_max": float(inst.y_sigma * torch.max(torch.abs(fmap_m - f64))),
+                    "rel_res_true_fp64_operator": res_m,
+                    "reference": "float64 GPU run of the same instance (float64 operator, fit, PCG and map)"}
 
     if rank != 0:
         if world > 1:
@@ -257,31 +304,41 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(inst, Zh, n_r, info["iterations"] if plain is None else plain["iterations"],
-                              finfo["iterations"])
+        cpu = oracle_baseline(cfg, ctx, L, to_dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x4+f32+f64", "data": "synthetic",
-        "config": {"workload": "single instance, n=16384 clustered, d=32, lambda=1e-4, 8 Tx, 512x512 grid, "
-                               "N_r=%d, tol 1e-6 true residual" % n_r,
-                   "n": n, "d": inst.d, "lambda": inst.lam, "n_r": n_r, "grid": CFG["grid"] ** 2,
-                   "operator": "matrix-free tcgen05 split-bf16 logits + ex2, double-float residual every 20 products",
-                   "l2": "working set larger than L2 (G kept as a 2 GiB float32 pair for true residuals)",
+        "vs_baseline": None, "dtype": "bf16 split (hi/lo) logits, f32 exp and sums, f64 scalars and residual",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"] + ", N_r=%d, tol %g true residual" % (n_r, cfg["tol"]),
+                   "n": n, "d": inst.d, "lambda": inst.lam, "n_r": n_r, "grid": cfg["grid"] ** 2,
+                   "operator": "matrix-free tcgen05 split-bf16 logits + ex2, float64-accurate residual every "
+                               "%d products" % cfg["refine_every"],
+                   "l2": "working set larger than L2 (129 MB): directions %.1f GB, float32 pair of G %.1f GB"
+                         % (n * n_r * 8 / 1e9, n * ldk * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "phases_ms_last_step": phases[-1] if phases else None,
         "solve": {"iterations": info["iterations"], "true_residuals": info["true_residuals"],
-                  "rel_res_true": info["rel_res_true"], "cccp_iterations": finfo["iterations"]},
+                  "rel_res_true": info["rel_res_true"], "cccp_iterations": finfo["iterations"],
+                  "eig_sweeps": finfo["eig_sweeps"]},
         "plain_fp64": plain,
+        "speedup_vs_plain_fp64": (value / plain["solves_per_s"]) if plain else None,
+        "accuracy_vs_fp64": accuracy,
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, row and column sums)", "bound": "tensor",
-                     "achieved": achieved, "peak": bf16_peak, "peak_kind": peak_kind + " bf16 burst",
-                     "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": MF_TRAFFIC_BYTES,
-                     "flops_per_launch": flops, "ms_per_launch": mv_ms,
-                     "tensor_bound_ms": t_tensor * 1e3, "sfu_bound_ms": t_sfu * 1e3,
-                     "frac_of_binding_roof": max(t_tensor, t_sfu) * 1e3 / mv_ms},
-        "materialised_fp32_matvec": {"ms_per_launch": mat_ms, "achieved_gbs": mat_gbs, "peak_gbs": hbm,
-                                     "frac": mat_gbs / hbm},
+        "roofline": {"kernel": "matrix-free product: k_mf_prep + k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, "
+                               "row and column sums) + k_mf_finish",
+                     "bound": bound, "achieved": achieved, "peak": bf16_peak,
+                     "peak_kind": peak_kind + " bf16 burst (kernel timed alone)", "unit": "TFLOP/s",
+                     "frac": achieved / bf16_peak, "traffic": MF_TRAFFIC_BYTES,
+                     "method_flops_per_product": flops, "unique_pairs": pairs,
+                     "ms_per_product": prod_ms, "ms_main_kernel": main_ms,
+                     "tensor_roof_ms": t_tensor * 1e3, "sfu_roof_ms": t_sfu * 1e3,
+                     "sfu_peak_ex2_per_s": sfu_peak,
+                     "frac_of_binding_roof": max(t_tensor, t_sfu) * 1e3 / prod_ms},
+        "materialised_fp32_matvec": {"ms_per_product": mat_ms, "achieved_gbs": mat_gbs, "peak_gbs": hbm,
+                                     "peak_kind": hbm_kind, "frac": mat_gbs / hbm,
+                                     "vs_matrix_free": mat_ms / prod_ms},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -490,69 +547,81 @@ def run_learned(args):
 # The FP64 oracle on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
 
-def oracle_baseline(inst, Z, n_r, pcg_iterations, cccp_iterations, budget_s: float = 25.0):
-    """Time the oracle's steps on a bounded sample and scale to one solve:
-    kernel build at full n; 5 PCG iterations at full n (dense matvec and dense
-    P apply) scaled by the iteration count; one dense CCCP iteration and the
-    dense Sigma^-1/2 at n_s = 2048 scaled by (n/n_s)^3 and the CCCP iteration
-    count; the map on 1/64 of the grid scaled by 64."""
+def oracle_solve(inst, Z, n_r, tol):
+    """One whole solve by the float64 oracle as it stands: kernel matrix,
+    random directions, dense shrinkage CCCP, Sigma_*^-1/2 by a dense
+    eigendecomposition, PCG to the tolerance and the map on the sample grid.
+    Returns the wall-clock seconds and the PCG / CCCP iteration counts."""
     from oracle import laker_oracle as O
-    n = inst.n
     t0 = time.perf_counter()
-    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
-    t_build = time.perf_counter() - t0
-    P = O.jacobi_preconditioner(A)       # a dense n x n stand-in with the cost of a dense P apply
-    t0 = time.perf_counter()
-    O.pcg(A, inst.y, P, 0.0, max_iter=5)
-    t_iter = (time.perf_counter() - t0) / 5
-    del P
-    ns = 2048
-    Us = O.random_directions(A[:ns, :ns], Z[:ns, :min(n_r, ns)])
-    t0 = time.perf_counter()
-    cc = O.cccp_fit(Us, 0.1, 0.1, 1e-8, max_iter=1)
-    t_cccp = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.inverse_sqrt(cc.Sigma)
-    t_eig = time.perf_counter() - t0
-    scale3 = (n / ns) ** 3
-    t_fit = (t_cccp * cccp_iterations + t_eig) * scale3
-    m = inst.Qg.shape[0]
-    ms_ = m // 64
-    t0 = time.perf_counter()
-    O.radio_map(inst.Qg[:ms_], inst.Q, np.zeros(n), inst.scale)
-    t_map = (time.perf_counter() - t0) * 64
-    total = t_build + t_fit + pcg_iterations * t_iter + t_map
-    return {"value": 1.0 / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": ("numpy float64 oracle: build at full n (%.2fs); 5 PCG iterations at full n (%.3fs each) x %d "
-                       "iterations; one dense CCCP iteration (%.2fs) and Sigma^-1/2 (%.2fs) at n=2048 scaled by "
-                       "(n/2048)^3 and %d CCCP iterations; map on 1/64 of the grid x 64 (%.2fs); estimated "
-                       "%.1fs per solve" % (t_build, t_iter, pcg_iterations, t_cccp, t_eig, cccp_iterations,
-                                            t_map, total))}
+    r = O.laker(inst.Q, inst.y, inst.lam, inst.scale, Z, tol=tol, Eg=inst.Qg)
+    dt = time.perf_counter() - t0
+    return dt, r.pcg.iterations, r.cccp.iterations
+
+
+def oracle_baseline(cfg, ctx=None, L=None, to_dev=None):
+    """The oracle timed on the host cores on a bounded sample of the workload:
+    one whole solve of an n = CPU_SAMPLE_N instance from the same generator
+    (same d, lambda, field and layout, N_r from the default schedule, map on a
+    CPU_SAMPLE_GRID^2 grid).  When the GPU library is at hand, the mixed GPU
+    path is timed on the same sample instance beside it."""
+    inst, Z, n_r = workload(cfg, cfg["seed"] + 77, n=CPU_SAMPLE_N, grid=CPU_SAMPLE_GRID)
+    dt, its, cits = oracle_solve(inst, Z, n_r, cfg["tol"])
+    out = {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "numpy float64 oracle, one whole solve (kernel, directions, dense CCCP, dense "
+                     "Sigma^-1/2, PCG to %g, map on a %dx%d grid) of an n=%d instance of the same generator "
+                     "(d=%d, N_r=%d): %.2f s, %d PCG products, %d CCCP iterations; BLAS threads = all cores"
+                     % (cfg["tol"], CPU_SAMPLE_GRID, CPU_SAMPLE_GRID, CPU_SAMPLE_N, cfg["d"], n_r, dt, its, cits)}
+    if L is not None:
+        import torch
+        Qd, yd, Zd, Qgd = to_dev(inst.Q), to_dev(inst.y), to_dev(Z), to_dev(inst.Qg)
+        times = []
+        for k in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op = L.laker_build_kernel(ctx, Qd, inst.scale, inst.lam, L.BF16X3)
+            P = L.laker_fit_preconditioner(ctx, op, Zd)
+            a, _ = L.laker_pcg_solve(ctx, op, P, yd, cfg["tol"], max_iter=40000, refine_every=cfg["refine_every"])
+            L.laker_eval_map(ctx, op, Qgd, a)
+            torch.cuda.synchronize()
+            if k > 0:
+                times.append(time.perf_counter() - t0)
+            P.close()
+            op.close()
+        out["gpu_same_sample"] = {"value": 1.0 / statistics.median(times), "unit": UNIT,
+                                  "note": "mixed GPU path on the same n=%d sample instance, median of 3" % CPU_SAMPLE_N}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the float64 oracle as it stands, on the host cores;
+    each step is one whole oracle solve of the bounded sample instance of the
+    workload (see oracle_baseline)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    inst, Zh, n_r = workload(SEED)
-    # iteration counts of the float64 method on this instance (measured on the
-    # GPU path; the oracle's own PCG needs the same order of iterations)
-    its, cccp_its = args.ref_iterations, args.ref_cccp_iterations
-    vals = []
+    cfg = SINGLE[args.workload if args.workload in SINGLE else "c3"]
+    inst, Z, n_r = workload(cfg, cfg["seed"] + 77, n=CPU_SAMPLE_N, grid=CPU_SAMPLE_GRID)
     for _ in range(args.warmup):
-        oracle_baseline(inst, Zh, n_r, its, cccp_its)
+        oracle_solve(inst, Z, n_r, cfg["tol"])
     t0 = time.perf_counter()
+    its = []
     for _ in range(args.steps):
-        vals.append(oracle_baseline(inst, Zh, n_r, its, cccp_its))
+        _, it, cit = oracle_solve(inst, Z, n_r, cfg["tol"])
+        its.append((it, cit))
     wall = time.perf_counter() - t0
-    v = statistics.median([b["value"] for b in vals])
+    v = args.steps / wall
+    sample = ("numpy float64 oracle, one whole solve per step (kernel, directions, dense CCCP, dense Sigma^-1/2, "
+              "PCG to %g, map on a %dx%d grid) of an n=%d instance of the workload's generator (d=%d, N_r=%d); "
+              "%d PCG products, %d CCCP iterations; %.1f s for %d steps"
+              % (cfg["tol"], CPU_SAMPLE_GRID, CPU_SAMPLE_GRID, CPU_SAMPLE_N, cfg["d"], n_r, its[-1][0], its[-1][1],
+                 wall, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single instance, n=16384 clustered, d=32, lambda=1e-4, 8 Tx, 512x512 grid"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": vals[-1]["sample"] + "; wall %.1fs for %d samples" % (wall, args.steps)},
+            "config": {"workload": cfg["name"] + " (bounded sample: n=%d of the same generator)" % CPU_SAMPLE_N},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -565,11 +634,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iterations", type=int, default=1500)
-    ap.add_argument("--ref-cccp-iterations", type=int, default=30)
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned"],
-                    help="single: the n=16384 instance (the headline line); batched: 256 instances; "
-                         "learned: the set-network preconditioner")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "batched", "learned"],
+                    help="c3: the precision-form instance n=65536, d=64 (the headline line); c2: the n=16384 "
+                         "instance; batched: 256 instances; learned: the set-network preconditioner")
     ap.add_argument("--learned-train", type=int, default=256)
     ap.add_argument("--learned-test", type=int, default=32)
     ap.add_argument("--learned-big", type=int, default=4)

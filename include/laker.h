@@ -125,6 +125,17 @@ laker_status laker_op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const doub
  * context's stream after one warm-up launch.  Used for roofline reporting.
  */
 laker_status laker_op_time_operator(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+/*
+ * Measurement hook (no counterpart in the paper): average device time in
+ * milliseconds of one whole product w = (lambda I + G) x as a PCG solve issues
+ * it -- for a matrix-free operator the preparation kernel, the tensor-core
+ * kernel and the finishing kernel; for a materialised one the streamed matvec
+ * -- over `reps` back-to-back products after one warm-up, timed with CUDA
+ * events on the context's stream with no synchronisation between products.
+ * Errors: LAKER_ERR_ARG for reps < 1 or NULL pointers; LAKER_ERR_TIMEOUT if a
+ * bounded wait of the tensor-core kernel expired.
+ */
+laker_status laker_op_time_product(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 
 /*
  * Preconditioner learning (Algorithm 1, learning stage; Sec. IV-B Eq.
@@ -355,9 +366,11 @@ laker_status laker_eval_map_method(laker_ctx* ctx, const laker_op* op, const dou
  * synchronise the device, as cudaMalloc and cudaFree do.  Scratch comes from a
  * static 32 MiB device array that every GPU loading this library keeps until
  * exit; its address is looked up on the first call per device (make that call
- * before any stream capture).  The call is asynchronous on the context's
- * stream.  All calls on a device share the array: calls that overlap on the
- * GPU race, so serialise them.
+ * before any stream capture; first calls from several host threads are
+ * serialised by a lock).  Nothing else is set up or uploaded: the kernels
+ * build their exp2 table in shared memory.  The call is asynchronous on the
+ * context's stream.  All calls on a device share the array: calls that
+ * overlap on the GPU race, so serialise them.
  * Errors: LAKER_ERR_ARG if the scratch needed, (m d + n d + n) * 8 bytes for
  * FP32/BF16X3 operators plus 8 m bytes of partial sums, exceeds 32 MiB.
  */

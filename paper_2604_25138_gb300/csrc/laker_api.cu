@@ -208,6 +208,13 @@ laker_status laker_op_time_operator(laker_ctx* ctx, const laker_op* op, const do
     return op_time_materialised(ctx, op, x, reps, ms);
 }
 
+laker_status laker_op_time_product(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !x || !ms || reps < 1) return set_error(ctx, LAKER_ERR_ARG, "bad arguments");
+    return op_time_product(ctx, op, x, reps, ms);
+}
+
 laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma,
                                       double rho, double eps, int max_iter, double tol, laker_precond** out,
                                       laker_fit_info* info) {

@@ -116,23 +116,21 @@ struct Dot3 {
     }
 };
 
-// 2^(j/64), j = 0..63, as double-float pairs.  Constant memory is per
-// translation unit: every unit that calls df_exp calls df_exp_init() on the
-// host before its first launch.
-static __constant__ float c_exp2_tab[128];
-
-inline cudaError_t df_exp_init() {
-    float h[128];
-    for (int j = 0; j < 64; ++j) {
+// 2^(j/64), j = 0..63, as double-float pairs (hi at 2j, lo at 2j + 1), built
+// by each thread block in its own shared memory from the float64 exp2 of the
+// math library: no host upload, so no ordering against other streams and no
+// set-up call.  The block must __syncthreads() before the first df_exp.
+__device__ __forceinline__ void df_exp_table_init(float* tab) {
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
         const double v = exp2((double)j / 64.0);
-        h[2 * j] = (float)v;
-        h[2 * j + 1] = (float)(v - (double)h[2 * j]);
+        const float h = (float)v;
+        tab[2 * j] = h;
+        tab[2 * j + 1] = (float)(v - (double)h);
     }
-    return cudaMemcpyToSymbol(c_exp2_tab, h, sizeof(h));
 }
 
 // e^x for a double-float x with |x| < 80; relative error ~1e-14.
-__device__ __forceinline__ df2 df_exp(df2 x) {
+__device__ __forceinline__ df2 df_exp(df2 x, const float* tab) {
     // ln2/64 = HI + MID + LO (residual < 2e-22); HI has 12 significant bits so
     // k * HI is exact for |k| < 2^12.  Values computed to 60 digits with sympy.
     constexpr float INV_LN2_64 = 92.33248138427734f;       // 64 / ln 2
@@ -155,7 +153,7 @@ __device__ __forceinline__ df2 df_exp(df2 x) {
     e = df_add(df2{1.f, 0.f}, e);
     const int j = k & 63;
     const int m = (k - j) / 64;
-    e = df_mul(e, df2{c_exp2_tab[2 * j], c_exp2_tab[2 * j + 1]});
+    e = df_mul(e, df2{tab[2 * j], tab[2 * j + 1]});
     return {ldexpf(e.hi, m), ldexpf(e.lo, m)};
 }
 

@@ -139,6 +139,7 @@ void mf_release(laker_op* op);
 laker_status mf_status(laker_ctx* ctx, const laker_op* op);
 laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+laker_status op_time_product(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 // laker_setnet.cu
 laker_status setnet_predict(laker_ctx* ctx, laker_setnet* s, int64_t n, const float* X, int nr, const float* F,
                             const float** logc, const float** logD);

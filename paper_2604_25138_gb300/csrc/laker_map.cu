@@ -8,6 +8,7 @@
 // float64 exp, per-row sums across the 16 column threads by shuffles, slices
 // summed afterwards in a fixed order.
 #include <algorithm>
+#include <mutex>
 
 #include "laker_device.cuh"
 #include "laker_df.cuh"
@@ -100,6 +101,8 @@ k_map_df(const float2* __restrict__ Qg_df, int64_t m, const float2* __restrict__
          const float2* __restrict__ alpha_df, int64_t tiles_per_slice, double* __restrict__ part) {
     __shared__ float2 qs[DF_TILE][DM];
     __shared__ float2 as[DF_TILE];
+    __shared__ float e2tab[128];
+    lk::df_exp_table_init(e2tab);   // ordered before its first use by the tile loop's barriers
     const int64_t row = (int64_t)blockIdx.x * DF_ROWS + threadIdx.x;
     lk::df2 g[DM];
 #pragma unroll
@@ -134,7 +137,7 @@ k_map_df(const float2* __restrict__ Qg_df, int64_t m, const float2* __restrict__
                     dot.add(g[t], lk::df2{q.x, q.y});
                 }
             }
-            const lk::df2 e = lk::df_exp(dot.value());
+            const lk::df2 e = lk::df_exp(dot.value(), e2tab);
             const float2 a = as[r];
             acc = lk::df_add(acc, lk::df_mul(e, lk::df2{a.x, a.y}));
         }
@@ -154,11 +157,6 @@ __global__ void k_to_df(int64_t count, const double* __restrict__ x, double scal
 
 static laker_status eval_map_df(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m, const double* alpha,
                                 double* out) {
-    static int table_ready_dev = -1;
-    if (table_ready_dev != ctx->device) {
-        LK_CUDA(ctx, lk::df_exp_init());
-        table_ready_dev = ctx->device;
-    }
     const int64_t n = op->n;
     const int d = op->d;
     float2 *qg = nullptr, *q = nullptr, *a = nullptr;
@@ -252,22 +250,19 @@ static __device__ __align__(256) unsigned char g_map_scratch[LAKER_MAP_SCRATCH_B
 namespace {
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
-bool g_table_ready[kMaxDevices] = {false};
+std::mutex g_scratch_mutex;   // first calls on a device from several host threads
 }  // namespace
 
 static laker_status noalloc_setup(laker_ctx* ctx, void** scratch) {
     if (ctx->device < 0 || ctx->device >= kMaxDevices)
         return set_error(ctx, LAKER_ERR_ARG, "device index out of range for the static scratch table");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (g_scratch_ptr[ctx->device] == nullptr) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_map_scratch);
         if (e != cudaSuccess)
             return set_error(ctx, LAKER_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch_ptr[ctx->device] = p;
-    }
-    if (!g_table_ready[ctx->device]) {
-        LK_CUDA(ctx, lk::df_exp_init());
-        g_table_ready[ctx->device] = true;
     }
     *scratch = g_scratch_ptr[ctx->device];
     return LAKER_OK;

@@ -816,6 +816,36 @@ laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const doub
     return st;
 }
 
+// Average device time of one whole product w = (lambda I + G) x as a solve
+// issues it (matrix-free: prep, tensor-core kernel and finish; materialised:
+// the streamed matvec), over `reps` back-to-back launches after one warm-up,
+// with CUDA events on the context's stream and no synchronisation between
+// the launches.
+laker_status op_time_product(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms) {
+    double* w = nullptr;
+    laker_status st = lk_malloc(ctx, (void**)&w, (size_t)op->n * sizeof(double));
+    if (st != LAKER_OK) return st;
+    cudaEvent_t e0, e1;
+    LK_CUDA(ctx, cudaEventCreate(&e0));
+    LK_CUDA(ctx, cudaEventCreate(&e1));
+    const bool mf = op->variant == LAKER_MATRIX_FREE;
+    for (int rep = -1; rep < reps && st == LAKER_OK; ++rep) {
+        if (rep == 0) LK_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        st = mf ? mf_matvec_launch(ctx, op, x, nullptr, nullptr, w, nullptr, nullptr, 0, nullptr, nullptr)
+                : op_matvec_inner(ctx, op, x, w);
+    }
+    LK_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    LK_CUDA(ctx, cudaEventSynchronize(e1));
+    float t = 0.f;
+    LK_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(w);
+    if (st != LAKER_OK) return st;
+    *ms = (double)t / reps;
+    return mf ? mf_status(ctx, op) : LAKER_OK;
+}
+
 laker_status pcg_prepare(laker_ctx* ctx) {
     LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)MV_SMEM_MAX));

@@ -86,6 +86,7 @@ def library() -> ctypes.CDLL:
         "laker_op_matvec": (i32, [vp, vp, vp, vp]),
         "laker_op_matvec_fp64": (i32, [vp, vp, vp, vp]),
         "laker_op_time_operator": (i32, [vp, vp, vp, i32, ctypes.POINTER(f64)]),
+        "laker_op_time_product": (i32, [vp, vp, vp, i32, ctypes.POINTER(f64)]),
         "laker_fit_preconditioner": (i32, [vp, vp, vp, i32, f64, f64, f64, i32, f64, pvp,
                                            ctypes.POINTER(FitInfo)]),
         "laker_precond_jacobi": (i32, [vp, vp, pvp]),
@@ -233,6 +234,15 @@ def laker_op_time_operator(ctx: Context, op: Operator, x: torch.Tensor, reps: in
     with ctx:
         ctx.check(library().laker_op_time_operator(ctx.handle, op.handle, _ptr(x, "x", op.n), reps,
                                                    ctypes.byref(ms)))
+    return ms.value
+
+
+def laker_op_time_product(ctx: Context, op: Operator, x: torch.Tensor, reps: int = 20) -> float:
+    """Average device milliseconds of one whole product as PCG issues it."""
+    ms = ctypes.c_double()
+    with ctx:
+        ctx.check(library().laker_op_time_product(ctx.handle, op.handle, _ptr(x, "x", op.n), reps,
+                                                  ctypes.byref(ms)))
     return ms.value
 
 

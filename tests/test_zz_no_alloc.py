@@ -62,3 +62,54 @@ def test_noalloc_map_refuses_oversized_requests(L):
     with pytest.raises(L.LakerError) as e:
         L.laker_eval_map_noalloc(ctx, op, Qg, dev(np.ones(64)), out)
     assert e.value.status == L.ERR_ARG
+
+
+def test_noalloc_map_at_the_scratch_edge_caps_the_slices(L):
+    """A double-float request that fills the static scratch to within 192
+    bytes: (m d + n d + n) * 8 bytes of inputs with m = 1000, d = 64,
+    n = 63527 is 33546040 bytes, 33546240 after 256-byte alignment, and the
+    partial sums take 8 m = 8000 more, 33554240 <= 32 MiB = 33554432.  Only one
+    slice of partial sums fits, so the slice count is capped by the scratch
+    (the allocating map takes ~76 slices here); the result must still match
+    the allocating map.  One more training point (n = 63528) needs
+    33554752 bytes and is refused."""
+    import torch
+    ctx = L.Context(0)
+    d, m = 64, 1000
+
+    def dev(x):
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+    inst = synth.make_instance(63528, d, 1e-3, seed=77, grid=32)
+    Qg = dev(inst.Qg[:m])
+    out = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda")
+    op_over = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP32)
+    alpha_over = dev(synth.random_vector(63528, 5))
+    with pytest.raises(L.LakerError) as e:
+        L.laker_eval_map_noalloc(ctx, op_over, Qg, alpha_over, out)
+    assert e.value.status == L.ERR_ARG
+    op_over.close()
+    n = 63527
+    op = L.laker_build_kernel(ctx, dev(inst.Q[:n]), inst.scale, inst.lam, L.FP32)
+    alpha = dev(synth.random_vector(n, 6) * 1e3)
+    ref = L.laker_eval_map(ctx, op, Qg, alpha, method=L.MAP_DOUBLE_FLOAT).cpu().numpy()
+    for call in range(2):
+        got = L.laker_eval_map_noalloc(ctx, op, Qg, alpha, out).cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10, call
+
+
+def test_noalloc_map_refuses_a_float64_request_over_4mi_rows(L):
+    """For a float64 operator the scratch holds only the partial sums, at
+    least 8 m bytes: m = 4 Mi + 1 query points need more than 32 MiB and are
+    refused before any work is issued."""
+    import torch
+    ctx = L.Context(0)
+    inst = synth.make_instance(64, 16, 1e-3, seed=4, grid=2)
+    op = L.laker_build_kernel(ctx, torch.as_tensor(inst.Q, device="cuda"), inst.scale, inst.lam, L.FP64)
+    m = (4 << 20) + 1
+    Qg = torch.zeros(m, 16, dtype=torch.float64, device="cuda")
+    out = torch.zeros(m, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LakerError) as e:
+        L.laker_eval_map_noalloc(ctx, op, Qg, torch.ones(64, dtype=torch.float64, device="cuda"), out)
+    assert e.value.status == L.ERR_ARG
