@@ -91,6 +91,13 @@ const char* laker_last_error(const laker_ctx* ctx);
 const char* laker_status_string(int status);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t laker_launch_count(const laker_ctx* ctx);
+/* Budget, in SM clock cycles, of each bounded device-side wait of the batched
+ * solver's grid barriers on this context (no counterpart in the paper); 0
+ * restores the default (~2 s).  A wait that runs out raises LAKER_ERR_TIMEOUT
+ * through the kernel's status word; every thread block then leaves at its
+ * next barrier and the context stays usable.  Errors: LAKER_ERR_ARG for
+ * cycles < 0. */
+laker_status laker_set_wait_budget(laker_ctx* ctx, int64_t cycles);
 
 /*
  * Kernel construction (Algorithm 1, kernel-construction stage; Sec. III-A,
@@ -163,6 +170,40 @@ laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const 
                                       int n_r, double gamma, double rho, double eps,
                                       int max_iter, double tol, laker_precond** P,
                                       laker_fit_info* info);
+/*
+ * laker_fit_preconditioner with the random directions drawn on the device from
+ * a seed instead of passed in (Sec. IV-B, Eq. random_directions: z_k ~ N(0, I_n)).
+ * Z is laker_random_directions(seed, n, n_r) in a workspace allocated and freed
+ * by the call; all other arguments, the result and the errors are those of
+ * laker_fit_preconditioner.
+ */
+laker_status laker_fit_preconditioner_seeded(laker_ctx* ctx, const laker_op* op, uint64_t seed, int n_r,
+                                             double gamma, double rho, double eps, int max_iter, double tol,
+                                             laker_precond** P, laker_fit_info* info);
+
+/*
+ * Gaussian random directions (Sec. IV-B, Eq. random_directions): Z (device,
+ * n x n_r float64, row-major, column k = z_k) with entries N(0, 1) from the
+ * counter-based generator Philox4x32-10 (Salmon et al., SC 2011) under the key
+ * seed: the pair of entries 2g, 2g + 1 of the row-major array is the
+ * Box-Muller transform of the two 53-bit uniforms
+ * u = ((x_a >> 6) 2^27 + (x_b >> 5) + 1/2) 2^-53 formed from the words
+ * (x0, x1) and (x2, x3) of the block at counter (g mod 2^32, g div 2^32, 0, 0):
+ * r cos(2 pi u2), r sin(2 pi u2) with r = sqrt(-2 ln u1).  Asynchronous.
+ * Errors: LAKER_ERR_ARG for n < 1, n_r < 1 or Z NULL.
+ */
+laker_status laker_random_directions(laker_ctx* ctx, uint64_t seed, int64_t n, int n_r, double* Z);
+
+/*
+ * The raw generator behind laker_random_directions (no counterpart in the
+ * paper; exposed so that its words can be checked bit for bit): out (device,
+ * 4 count uint32) receives the Philox4x32-10 blocks of the counters
+ * counter0 .. counter0 + count - 1 (64-bit counter in words c0, c1; c2 = c3
+ * = 0) under the 64-bit key.  Asynchronous.
+ * Errors: LAKER_ERR_ARG for count < 0 or out NULL.
+ */
+laker_status laker_philox4x32_10(laker_ctx* ctx, uint64_t key, uint64_t counter0, int64_t count, uint32_t* out);
+
 /* Jacobi preconditioner P_J = diag(lambda I + G)^-1 (Sec. V-A baselines). */
 laker_status laker_precond_jacobi(laker_ctx* ctx, const laker_op* op, laker_precond** P);
 laker_status laker_precond_destroy(laker_precond* P);
@@ -210,6 +251,23 @@ laker_status laker_pcg_solve_trace(laker_ctx* ctx, const laker_op* op, const lak
                                    int refine_every, laker_solve_info* info, double* trace, int trace_cap);
 
 /*
+ * laker_pcg_solve that stops on the paper's objective gap (Sec. V-A,
+ * Eq. iterations with TAR.TOL = gap): after product k the objective
+ * R(alpha_k) = |G alpha_k - y|^2 + lambda alpha_k^T G alpha_k (Eq.
+ * simu-R-definition, formed from the recursive residual as in
+ * laker_pcg_solve_trace) is compared with the reference R_ref, and the solve
+ * stops at the first k with |R(alpha_k) - R_ref| <= gap |R_ref|, or when the
+ * residual test with `tol` holds (tol = 0 disables it), or at max_iter.
+ * info->iterations is that k.  R_ref comes from a reference solution (the
+ * paper's convex-solver solution; a tight PCG solve serves).
+ * Errors: as laker_pcg_solve; LAKER_ERR_ARG for gap <= 0 or R_ref zero or
+ * not finite.
+ */
+laker_status laker_pcg_solve_gap(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
+                                 double* alpha, double R_ref, double gap, double tol, int max_iter, int refine_every,
+                                 laker_solve_info* info);
+
+/*
  * Extreme eigenvalues of the Lanczos tridiagonal T_k of k PCG products (host
  * arithmetic on a trace of laker_pcg_solve_trace): T_jj = 1/delta_j +
  * beta_{j-1}/delta_{j-1}, T_j,j+1 = sqrt(beta_j)/delta_j.  Its eigenvalues are
@@ -228,6 +286,44 @@ laker_status laker_lanczos_extremes(const double* trace, int k, double* lmin, do
  * reaches it.
  */
 int laker_trace_gap_iterations(const double* trace, int k_max, double R_ref, double gap);
+
+/*
+ * Gradient descent on R(alpha) (Sec. V-A, the first-order baseline of the
+ * numerical-layer comparison; Eq. simu-R-definition):
+ *   alpha^0 = 0;  alpha^{k+1} = alpha^k - eta grad R(alpha^k),
+ *   grad R(alpha) = 2 G ((lambda I + G) alpha - y),
+ * two operator products per step.  The paper selects eta by grid search;
+ * eta <= 0 here selects eta = 1 / (2 mu (mu + lambda)) with mu = lambda_max(G)
+ * from 50 power-iteration products (laker_op_lambda_max), the largest step
+ * that contracts every eigen-component of the error; a caller's grid search
+ * passes multiples of it.  *eta_used (host, may be NULL) receives the step.
+ * Stops when |y - (lambda I + G) alpha^k| / |y| <= tol (tested every 16
+ * steps) or after max_iter steps; alpha (device, n) receives the last iterate.
+ * trace (host, 2 trace_cap doubles, may be NULL): for k = 1 .. min(steps,
+ * trace_cap), |r_k|^2 / |y|^2 and R(alpha_k) of the iterate after k steps.
+ * Errors: LAKER_ERR_ARG for NULL pointers, max_iter < 0, tol < 0;
+ * LAKER_ERR_MAXITER if tol was not reached (alpha still written);
+ * LAKER_ERR_BREAKDOWN if the iterates overflow.
+ */
+laker_status laker_gd_solve(laker_ctx* ctx, const laker_op* op, const double* y, double* alpha, double eta,
+                            double tol, int max_iter, double* eta_used, laker_solve_info* info, double* trace,
+                            int trace_cap);
+
+/* lambda_max(G) (host *mu) by `iters` power-iteration products with the
+ * operator's inner precision, from the all-ones start (no counterpart in the
+ * paper; the step-size rule of laker_gd_solve).  Errors: LAKER_ERR_ARG for
+ * iters < 1 or NULL pointers. */
+laker_status laker_op_lambda_max(laker_ctx* ctx, const laker_op* op, int iters, double* mu);
+
+/*
+ * Prediction discrepancy (Sec. V-A, Eq. prediction-discrepancy):
+ * *out (host) = |G alpha - G alpha_ref| / |G alpha_ref| with the operator's
+ * float64-accurate product (G x = (lambda I + G) x - lambda x).  alpha and
+ * alpha_ref are device n-vectors.  Synchronous.
+ * Errors: LAKER_ERR_ARG for NULL pointers or G alpha_ref = 0.
+ */
+laker_status laker_prediction_discrepancy(laker_ctx* ctx, const laker_op* op, const double* alpha,
+                                          const double* alpha_ref, double* out);
 
 /* One instance of a batched solve: its operator, preconditioner (NULL =
  * identity), right-hand side y (device, n) and output alpha (device, n). */
@@ -293,6 +389,19 @@ int64_t laker_setnet_num_params(const laker_setnet* net);
 /* host float32 arrays of laker_setnet_num_params entries; set resets Adam */
 laker_status laker_setnet_get_params(laker_ctx* ctx, const laker_setnet* net, float* host);
 laker_status laker_setnet_set_params(laker_ctx* ctx, laker_setnet* net, const float* host);
+/*
+ * Checkpoint of a set network (no counterpart in the paper): laker_setnet_save
+ * writes the sizes, the Adam step count, the float32 weights and both Adam
+ * moments to the file `path` (created or replaced; 8-byte magic "LAKERSN1",
+ * int32 in_dim, hidden, dir_hidden, step, int64 parameter count, then three
+ * float32 arrays of that count, host byte order); laker_setnet_load creates a
+ * network from such a file, so that training resumes exactly where it stopped.
+ * Both synchronise the context's stream.
+ * Errors: LAKER_ERR_ARG for NULL pointers, a file that cannot be opened,
+ * written or read, or one that is not a checkpoint of consistent sizes.
+ */
+laker_status laker_setnet_save(laker_ctx* ctx, const laker_setnet* net, const char* path);
+laker_status laker_setnet_load(laker_ctx* ctx, const char* path, laker_setnet** net);
 /* X (device, n x (d + 3) float32) = [loc (n x 2), Q (n x d), y (n)] (device float64 inputs) */
 laker_status laker_setnet_point_features(laker_ctx* ctx, int64_t n, int d, const double* loc, const double* Q,
                                          const double* y, float* X);

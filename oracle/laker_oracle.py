@@ -25,6 +25,9 @@ Paper map (arXiv 2604.25138):
 * Sec. IV-E and Algorithm 1 (PCG stage): preconditioned conjugate gradient.
 * Sec. V-A, Eqs. (simu-R-definition, residual, objective-gap,
   prediction-discrepancy, rmse, nmse): evaluation metrics.
+* Sec. V-A, numerical-layer baselines: gradient descent on R(alpha).
+* oracle/philox.py: the counter-based generator behind the device-drawn
+  random directions (Philox4x32-10, Salmon et al. 2011).
 
 Parity pins (see tests/test_oracle_pins.py): every function below is pinned by
 a test that does not re-run its own formula -- the paper's Example 1, exact
@@ -265,6 +268,46 @@ def rmse(pred: np.ndarray, truth: np.ndarray) -> float:
 def nmse(pred: np.ndarray, truth: np.ndarray) -> float:
     """Eq. nmse."""
     return float(np.sum((pred - truth) ** 2) / np.sum(truth ** 2))
+
+
+def gradient_R(G: np.ndarray, alpha: np.ndarray, y: np.ndarray, lam: float) -> np.ndarray:
+    """grad R(alpha) = 2 G (G alpha - y) + 2 lambda G alpha: the gradient of
+    R(alpha) = |G alpha - y|^2 + lambda alpha^T G alpha (Eq. simu-R-definition)
+    for a symmetric G."""
+    Ga = G @ alpha
+    return 2.0 * (G @ (Ga - y)) + 2.0 * lam * Ga
+
+
+@dataclasses.dataclass
+class GDResult:
+    alpha: np.ndarray
+    steps: int                 # gradient steps taken
+    converged: bool
+    rel_res: list              # |y - (lambda I + G) alpha^k| / |y| for k = 1 .. steps
+    R: list                    # R(alpha^k) for k = 1 .. steps
+
+
+def gradient_descent(G: np.ndarray, y: np.ndarray, lam: float, eta: float, max_iter: int,
+                     tol: float = 0.0) -> GDResult:
+    """The first-order baseline of Sec. V-A: alpha^0 = 0 and
+    alpha^{k+1} = alpha^k - eta grad R(alpha^k); stop once the relative
+    residual |y - (lambda I + G) alpha^k| / |y| <= tol or after max_iter
+    steps.  (The paper tunes eta by grid search.)"""
+    n = y.shape[0]
+    alpha = np.zeros(n)
+    A = G + lam * np.eye(n)
+    ny = float(np.linalg.norm(y))
+    res, Rs = [], []
+    if ny == 0.0 or float(np.linalg.norm(y - A @ alpha)) <= tol * ny:
+        return GDResult(alpha=alpha, steps=0, converged=True, rel_res=res, R=Rs)
+    for k in range(1, max_iter + 1):
+        alpha = alpha - eta * gradient_R(G, alpha, y, lam)
+        rel = float(np.linalg.norm(y - A @ alpha)) / ny
+        res.append(rel)
+        Rs.append(objective_R(G, alpha, y, lam))
+        if rel <= tol:
+            return GDResult(alpha=alpha, steps=k, converged=True, rel_res=res, R=Rs)
+    return GDResult(alpha=alpha, steps=max_iter, converged=False, rel_res=res, R=Rs)
 
 
 def condition_number(A: np.ndarray, P: np.ndarray | None = None) -> float:

@@ -236,6 +236,31 @@ laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const 
     return LAKER_OK;
 }
 
+laker_status laker_fit_preconditioner_seeded(laker_ctx* ctx, const laker_op* op, uint64_t seed, int n_r,
+                                             double gamma, double rho, double eps, int max_iter, double tol,
+                                             laker_precond** out, laker_fit_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (n_r < 1 || n_r > LK_MAX_NR) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 2048");
+    if (!(gamma >= 0.0) || !(eps > 0.0) || rho > 1.0 || max_iter < 1 || !(tol >= 0.0))
+        return set_error(ctx, LAKER_ERR_ARG, "bad CCCP parameters");
+    double* Z = nullptr;
+    if ((st = lk_malloc(ctx, (void**)&Z, (size_t)op->n * n_r * sizeof(double))) != LAKER_OK) return st;
+    if ((st = random_directions(ctx, seed, op->n * (int64_t)n_r, Z)) != LAKER_OK) { cudaFree(Z); return st; }
+    laker_precond* P = new (std::nothrow) laker_precond();
+    if (!P) { cudaFree(Z); return LAKER_ERR_OOM; }
+    P->ctx = ctx;
+    P->use32 = op->precision != LAKER_FP64;
+    st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(Z);
+    if (st != LAKER_OK) { free_precond(P); return st; }
+    *out = P;
+    return LAKER_OK;
+}
+
 laker_status laker_fit_preconditioner_learned(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
                                               double gamma, double rho, double eps, int max_iter, double tol,
                                               laker_setnet* net, const float* X, int mode, laker_precond** out,
@@ -338,6 +363,27 @@ laker_status laker_pcg_solve_trace(laker_ctx* ctx, const laker_op* op, const lak
     if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
     if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
     return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info, trace, trace_cap);
+}
+
+laker_status laker_pcg_solve_gap(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
+                                 double* alpha, double R_ref, double gap, double tol, int max_iter, int refine_every,
+                                 laker_solve_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !y || !alpha) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (!(gap > 0.0) || !std::isfinite(R_ref) || R_ref == 0.0)
+        return set_error(ctx, LAKER_ERR_ARG, "need gap > 0 and a finite, nonzero R_ref");
+    if (!(tol >= 0.0) || max_iter < 1 || refine_every < 0) return set_error(ctx, LAKER_ERR_ARG, "bad PCG parameters");
+    if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
+    if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
+    return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info, nullptr, 0, R_ref, gap);
+}
+
+laker_status laker_set_wait_budget(laker_ctx* ctx, int64_t cycles) {
+    if (!ctx) return LAKER_ERR_ARG;
+    if (cycles < 0) return set_error(ctx, LAKER_ERR_ARG, "wait budget must be >= 0");
+    ctx->wait_cycles = cycles;
+    return LAKER_OK;
 }
 
 // Number of eigenvalues of the symmetric tridiagonal (a, b) below x: the

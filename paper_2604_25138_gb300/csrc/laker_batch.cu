@@ -80,6 +80,7 @@ struct BArgs {
     int max_iter;
     int refine_every;
     int mixed;             // 1: float32 product + float64-accurate true residual
+    long long spin;        // budget of each grid-barrier wait, in clock cycles
 };
 
 constexpr int KB = BW;     // directions per direction item (one per warp)
@@ -513,7 +514,7 @@ k_batch_pcg(BArgs a, double tol) {
     __shared__ double ts[LK_MAX_NR];
     BGlobal* g = a.g;
     int* err = &g->err;
-    auto sync = [&]() { return lk::grid_sync(&g->gs, err); };
+    auto sync = [&]() { return lk::grid_sync(&g->gs, err, a.spin); };
     if (blockIdx.x == 0 && threadIdx.x == 0) g->t0 = globaltimer();
     ph_init(a, red);
     if (!sync()) return;
@@ -618,6 +619,7 @@ static laker_status batch_launch(laker_ctx* ctx, const std::vector<BInst>& hin, 
     a.max_iter = max_iter;
     a.refine_every = refine_every;
     a.mixed = fp64_prec ? 0 : 1;
+    a.spin = ctx->wait_cycles > 0 ? (long long)ctx->wait_cycles : lk::GRID_SPIN_CYCLES;
     const void* fn = fp64_prec ? (const void*)k_batch_pcg<double> : (const void*)k_batch_pcg<float>;
     int occ = 0;
     LK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT, 0));

@@ -73,7 +73,7 @@ struct GridSync {
     unsigned int gen;
 };
 constexpr long long GRID_SPIN_CYCLES = 4000000000ll;
-__device__ __forceinline__ bool grid_sync(GridSync* gs, int* err) {
+__device__ __forceinline__ bool grid_sync(GridSync* gs, int* err, long long budget = GRID_SPIN_CYCLES) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -89,7 +89,7 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int* err) {
             for (unsigned int spins = 1; *genp == g; ++spins) {
                 if ((spins & 63u) == 0) {
                     if (*(volatile int*)err) break;
-                    if (clock64() - t0 > GRID_SPIN_CYCLES) {
+                    if (clock64() - t0 > budget) {
                         atomicExch(err, LAKER_ERR_TIMEOUT);
                         break;
                     }

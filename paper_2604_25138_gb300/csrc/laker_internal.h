@@ -30,6 +30,8 @@ struct PcgScalars {
     double* trace;      // per product k: delta, |r|^2/|y|^2, R(alpha), beta (4 doubles), or null
     int trace_cap;      // products the trace holds
     int pad2;
+    double R_ref;       // reference objective of the gap stop
+    double gap_tol;     // > 0: stop once |R(alpha) - R_ref| <= gap_tol |R_ref|
 };
 
 struct laker_ctx {
@@ -39,6 +41,7 @@ struct laker_ctx {
     int num_sms = 0;
     int64_t launches = 0;
     void* cublas = nullptr;     // cuBLAS handle for the fit's plain products, created on first use
+    int64_t wait_cycles = 0;    // budget of bounded device waits (0 = the default, ~2 s)
     std::string last_error;
 };
 
@@ -119,7 +122,7 @@ laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x,
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
                        const double* y, double* alpha, double tol, int max_iter,
                        int refine_every, laker_solve_info* info, double* trace = nullptr,
-                       int trace_cap = 0);
+                       int trace_cap = 0, double R_ref = 0.0, double gap_tol = 0.0);
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
 // laker_fit.cu
 void release_cublas(laker_ctx* ctx);
@@ -140,6 +143,8 @@ laker_status mf_status(laker_ctx* ctx, const laker_op* op);
 laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_product(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+// laker_rng.cu (Philox4x32-10 Gaussian directions, n_r-major rows)
+laker_status random_directions(laker_ctx* ctx, uint64_t seed, int64_t count, double* Z);
 // laker_setnet.cu
 laker_status setnet_predict(laker_ctx* ctx, laker_setnet* s, int64_t n, const float* X, int nr, const float* F,
                             const float** logc, const float** logD);

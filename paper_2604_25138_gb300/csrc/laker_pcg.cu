@@ -299,6 +299,8 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
     row_range(n, r0, r1);
     const double delta = sc->delta;
     double* trace = sc->trace;   // uniform: the trace also needs r.alpha and y.alpha
+    const bool gap = sc->gap_tol > 0.0;   // uniform: so does the objective-gap stop
+    const bool objective = trace != nullptr || gap;
     double rr = 0.0, ra = 0.0, ya = 0.0;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         const double ai = fma(delta, p[i], alpha[i]);
@@ -306,14 +308,14 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
         const double ri = fma(-delta, w[i], r[i]);
         r[i] = ri;
         rr = fma(ri, ri, rr);
-        if (trace) {
+        if (objective) {
             ra = fma(ri, ai, ra);
             ya = fma(y[i], ai, ya);
         }
     }
     rr = lk::block_sum(rr, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = rr;
-    if (trace) {
+    if (objective) {
         ra = lk::block_sum(ra, red);
         ya = lk::block_sum(ya, red);
         if (threadIdx.x == 0) {
@@ -324,7 +326,7 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
     if (lk::last_block(&sc->ticket[2])) {
         const double tot = lk::sum_partials(partials, gridDim.x, red);
         double tra = 0.0, tya = 0.0;
-        if (trace) {
+        if (objective) {
             tra = lk::sum_partials(partials + gridDim.x, gridDim.x, red);
             tya = lk::sum_partials(partials + 2 * gridDim.x, gridDim.x, red);
         }
@@ -333,14 +335,17 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
             const int it = sc->iters;
             // R(alpha) = |G alpha - y|^2 + lambda alpha^T G alpha with G alpha = y - r - lambda alpha
             // (Eq. simu-R-definition) is |r|^2 + lambda (r.alpha + y.alpha)
+            const double R = fma(lambda, tra + tya, tot);
             if (trace && it >= 1 && it <= sc->trace_cap) {
                 trace[4 * (it - 1)] = delta;
                 trace[4 * (it - 1) + 1] = tot / sc->yy;
-                trace[4 * (it - 1) + 2] = fma(lambda, tra + tya, tot);
+                trace[4 * (it - 1) + 2] = R;
             }
             const bool small = tot <= sc->tol2yy;
             if (!isfinite(tot)) {
                 sc->converged = 2;
+            } else if (gap && fabs(R - sc->R_ref) <= sc->gap_tol * fabs(sc->R_ref)) {
+                sc->converged = 1;   // objective gap reached (Eq. iterations, TAR.TOL)
             } else if (sc->refine_every == 0) {
                 if (small) sc->converged = 1;
                 else if (it >= sc->max_iter) sc->converged = 3;
@@ -894,7 +899,7 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
 
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
                        double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info,
-                       double* trace, int trace_cap) {
+                       double* trace, int trace_cap, double R_ref, double gap_tol) {
     const int64_t n = op->n;
     const bool mixed = (op->precision != LAKER_FP64) && refine_every > 0;
     const bool use32 = (op->precision != LAKER_FP64);
@@ -910,6 +915,8 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     PcgScalars init{};
     init.max_iter = max_iter;
     init.refine_every = mixed ? refine_every : 0;
+    init.R_ref = R_ref;
+    init.gap_tol = gap_tol;
     struct TraceBuf {
         double* p = nullptr;
         ~TraceBuf() { cudaFree(p); }

@@ -16,6 +16,9 @@
 // layers run through one tiled GEMM kernel with fused bias + tanh or
 // tanh-derivative epilogues; every reduction is in a fixed order.
 #include <cuda_bf16.h>
+#include <string>
+#include <cstring>
+#include <cstdio>
 
 #include <algorithm>
 #include <cmath>
@@ -625,6 +628,79 @@ laker_status laker_setnet_train_step(laker_ctx* ctx, laker_setnet* net, int B, c
     if ((st = setnet_forward(ctx, net, B, X, poff, F, koff)) != LAKER_OK) return st;
     if ((st = setnet_backward(ctx, net, tc, tD, loss)) != LAKER_OK) return st;
     return setnet_adam(ctx, net, lr);
+}
+
+// Checkpoint file: 8-byte magic "LAKERSN1", int32 in_dim, hidden,
+// dir_hidden, Adam step, int64 parameter count, then float32 weights, Adam
+// first and second moments (parameter count each), little-endian as written
+// by the host.
+static const char kSnMagic[8] = {'L', 'A', 'K', 'E', 'R', 'S', 'N', '1'};
+
+laker_status laker_setnet_save(laker_ctx* ctx, const laker_setnet* net, const char* path) {
+    if (!ctx) return LAKER_ERR_ARG;
+    if (!net || !path) return set_error(ctx, LAKER_ERR_ARG, "set network save: null argument");
+    std::vector<float> buf((size_t)3 * net->np);
+    LK_CUDA(ctx, cudaMemcpyAsync(buf.data(), net->theta, sizeof(float) * net->np, cudaMemcpyDeviceToHost, ctx->stream));
+    LK_CUDA(ctx, cudaMemcpyAsync(buf.data() + net->np, net->m, sizeof(float) * net->np, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    LK_CUDA(ctx, cudaMemcpyAsync(buf.data() + 2 * net->np, net->v, sizeof(float) * net->np, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(ctx, LAKER_ERR_ARG, std::string("set network save: cannot open ") + path);
+    const int32_t hdr[4] = {net->in_dim, net->H, net->Hd, net->step};
+    const int64_t np = net->np;
+    bool ok = std::fwrite(kSnMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(&np, sizeof(np), 1, f) == 1 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LAKER_OK : set_error(ctx, LAKER_ERR_ARG, std::string("set network save: write failed: ") + path);
+}
+
+laker_status laker_setnet_load(laker_ctx* ctx, const char* path, laker_setnet** net) {
+    if (!ctx) return LAKER_ERR_ARG;
+    if (!net || !path) return set_error(ctx, LAKER_ERR_ARG, "set network load: null argument");
+    *net = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(ctx, LAKER_ERR_ARG, std::string("set network load: cannot open ") + path);
+    char magic[8];
+    int32_t hdr[4];
+    int64_t np = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSnMagic, 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&np, sizeof(np), 1, f) == 1 &&
+              hdr[0] >= 1 && hdr[1] >= 1 && hdr[2] >= 1 && hdr[3] >= 0 && np >= 1;
+    std::vector<float> buf;
+    if (ok) {
+        buf.resize((size_t)3 * np);
+        ok = std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    }
+    std::fclose(f);
+    if (!ok) return set_error(ctx, LAKER_ERR_ARG, std::string("set network load: not a set-network checkpoint: ") + path);
+    laker_setnet* s = nullptr;
+    laker_status st = setnet_create(ctx, hdr[0], hdr[1], hdr[2], 0, &s);
+    if (st != LAKER_OK) return st;
+    if (s->np != np) {
+        setnet_destroy(s);
+        return set_error(ctx, LAKER_ERR_ARG, "set network load: parameter count does not match the sizes");
+    }
+    cudaError_t e = cudaMemcpyAsync(s->theta, buf.data(), sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->m, buf.data() + np, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->v, buf.data() + 2 * np, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        k_sn_to_bf16<<<gsz(np), 256, 0, ctx->stream>>>(np, s->theta, s->wbf);
+        ctx->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        setnet_destroy(s);
+        return set_error(ctx, LAKER_ERR_CUDA, std::string("set network load: ") + cudaGetErrorString(e));
+    }
+    s->step = hdr[3];
+    *net = s;
+    return LAKER_OK;
 }
 
 }  // extern "C"

@@ -101,6 +101,18 @@ def library() -> ctypes.CDLL:
         "laker_eval_map": (i32, [vp, vp, vp, i64, vp, vp]),
         "laker_eval_map_method": (i32, [vp, vp, vp, i64, vp, vp, i32]),
         "laker_eval_map_noalloc": (i32, [vp, vp, vp, i64, vp, vp]),
+        "laker_fit_preconditioner_seeded": (i32, [vp, vp, ctypes.c_uint64, i32, f64, f64, f64, i32, f64, pvp,
+                                                  ctypes.POINTER(FitInfo)]),
+        "laker_random_directions": (i32, [vp, ctypes.c_uint64, i64, i32, vp]),
+        "laker_philox4x32_10": (i32, [vp, ctypes.c_uint64, ctypes.c_uint64, i64, vp]),
+        "laker_pcg_solve_gap": (i32, [vp, vp, vp, vp, vp, f64, f64, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
+        "laker_set_wait_budget": (i32, [vp, i64]),
+        "laker_gd_solve": (i32, [vp, vp, vp, vp, f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(SolveInfo),
+                                 ctypes.POINTER(f64), i32]),
+        "laker_op_lambda_max": (i32, [vp, vp, i32, ctypes.POINTER(f64)]),
+        "laker_prediction_discrepancy": (i32, [vp, vp, vp, vp, ctypes.POINTER(f64)]),
+        "laker_setnet_save": (i32, [vp, vp, ctypes.c_char_p]),
+        "laker_setnet_load": (i32, [vp, ctypes.c_char_p, pvp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -262,13 +274,31 @@ def laker_fit_preconditioner(ctx: Context, op: Operator, Z: torch.Tensor, gamma:
 class SetNet:
     """Handle of the learned set-to-parameters network (device weights)."""
 
-    def __init__(self, ctx: Context, in_dim: int, hidden: int = 256, dir_hidden: int = 64, seed: int = 0):
+    def __init__(self, ctx: Context, in_dim: int, hidden: int = 256, dir_hidden: int = 64, seed: int = 0,
+                 _handle=None):
         self.ctx = ctx
         self.in_dim, self.hidden, self.dir_hidden = in_dim, hidden, dir_hidden
+        if _handle is not None:
+            self.handle = _handle
+            return
         h = ctypes.c_void_p()
         with ctx:
             ctx.check(library().laker_setnet_create(ctx.handle, in_dim, hidden, dir_hidden, seed, ctypes.byref(h)))
         self.handle = h
+
+    def save(self, path: str):
+        """laker_setnet_save: weights, Adam moments and step to a file."""
+        with self.ctx:
+            self.ctx.check(library().laker_setnet_save(self.ctx.handle, self.handle, os.fsencode(path)))
+
+    @staticmethod
+    def load(ctx: Context, path: str, in_dim: int, hidden: int = 256, dir_hidden: int = 64) -> "SetNet":
+        """laker_setnet_load: a network restored from a checkpoint file (the
+        sizes given here must be those stored in it)."""
+        h = ctypes.c_void_p()
+        with ctx:
+            ctx.check(library().laker_setnet_load(ctx.handle, os.fsencode(path), ctypes.byref(h)))
+        return SetNet(ctx, in_dim, hidden, dir_hidden, _handle=h)
 
     def num_params(self) -> int:
         return int(library().laker_setnet_num_params(self.handle))
@@ -515,3 +545,84 @@ def laker_eval_map_noalloc(ctx: Context, op: Operator, Qg: torch.Tensor, alpha: 
         ctx.check(library().laker_eval_map_noalloc(ctx.handle, op.handle, _ptr(Qg, "Qg", m * op.d), m,
                                                    _ptr(alpha, "alpha", op.n), _ptr(out, "out", m)))
     return out
+
+
+def laker_fit_preconditioner_seeded(ctx: Context, op: Operator, seed: int, n_r: int, gamma: float = 0.1,
+                                    rho: float = -1.0, eps: float = 1e-8, max_iter: int = 200,
+                                    tol: float = 1e-10) -> Preconditioner:
+    """CCCP fit with the random directions drawn on the device from `seed`."""
+    info = FitInfo()
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_fit_preconditioner_seeded(ctx.handle, op.handle, seed, n_r, gamma, rho, eps,
+                                                            max_iter, tol, ctypes.byref(h), ctypes.byref(info)))
+    d = {f: getattr(info, f) for f, _ in FitInfo._fields_}
+    return Preconditioner(ctx, h, op.n, n_r, d)
+
+
+def laker_random_directions(ctx: Context, seed: int, n: int, n_r: int) -> torch.Tensor:
+    Z = torch.empty((n, n_r), dtype=torch.float64, device=torch.device("cuda", ctx.device))
+    with ctx:
+        ctx.check(library().laker_random_directions(ctx.handle, seed, n, n_r, Z.data_ptr()))
+    return Z
+
+
+def laker_philox4x32_10(ctx: Context, key: int, counter0: int, count: int) -> torch.Tensor:
+    """Raw Philox4x32-10 words (count blocks of 4) as an int64 tensor of uint32 values."""
+    out = torch.empty(4 * count, dtype=torch.int32, device=torch.device("cuda", ctx.device))
+    with ctx:
+        ctx.check(library().laker_philox4x32_10(ctx.handle, key, counter0, count, out.data_ptr()))
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def laker_pcg_solve_gap(ctx: Context, op: Operator, P: Preconditioner | None, y: torch.Tensor, R_ref: float,
+                        gap: float = 1e-3, tol: float = 0.0, max_iter: int = 100000, refine_every: int = 0,
+                        allow_maxiter: bool = False):
+    alpha = torch.empty_like(y)
+    info = SolveInfo()
+    with ctx:
+        st = library().laker_pcg_solve_gap(ctx.handle, op.handle, P.handle if P is not None else None,
+                                           _ptr(y, "y", op.n), _ptr(alpha, "alpha", op.n), R_ref, gap, tol,
+                                           max_iter, refine_every, ctypes.byref(info))
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    return alpha, {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+
+def laker_set_wait_budget(ctx: Context, cycles: int):
+    ctx.check(library().laker_set_wait_budget(ctx.handle, int(cycles)))
+
+
+def laker_gd_solve(ctx: Context, op: Operator, y: torch.Tensor, eta: float = 0.0, tol: float = 0.0,
+                   max_iter: int = 1000, trace_cap: int = 0, allow_maxiter: bool = True):
+    """Gradient descent on R(alpha); returns (alpha, info, eta_used, trace)
+    with trace a (steps x 2) array of |r|^2/|y|^2 and R(alpha) (or None)."""
+    import numpy as np
+    alpha = torch.empty_like(y)
+    info = SolveInfo()
+    eu = ctypes.c_double()
+    tr = np.zeros(2 * max(1, trace_cap), dtype=np.float64) if trace_cap > 0 else None
+    with ctx:
+        st = library().laker_gd_solve(ctx.handle, op.handle, _ptr(y, "y", op.n), _ptr(alpha, "alpha", op.n), eta,
+                                      tol, max_iter, ctypes.byref(eu), ctypes.byref(info),
+                                      tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if tr is not None else None,
+                                      trace_cap)
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    d = {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+    if tr is not None:
+        tr = tr.reshape(trace_cap, 2)[:min(d["iterations"], trace_cap)].copy()
+    return alpha, d, eu.value, tr
+
+
+def laker_op_lambda_max(ctx: Context, op: Operator, iters: int = 50) -> float:
+    mu = ctypes.c_double()
+    with ctx:
+        ctx.check(library().laker_op_lambda_max(ctx.handle, op.handle, iters, ctypes.byref(mu)))
+    return mu.value
+
+
+def laker_prediction_discrepancy(ctx: Context, op: Operator, alpha: torch.Tensor, alpha_ref: torch.Tensor) -> float:
+    out = ctypes.c_double()
+    with ctx:
+        ctx.check(library().laker_prediction_discrepancy(ctx.handle, op.handle, _ptr(alpha, "alpha", op.n),
+                                                         _ptr(alpha_ref, "alpha_ref", op.n), ctypes.byref(out)))
+    return out.value

@@ -486,3 +486,71 @@ def test_condition_number_of_a_known_spectrum():
 def scipy_eigh_general(A, B):
     import scipy.linalg
     return scipy.linalg.eigh(A, 0.5 * (B + B.T), eigvals_only=True)
+
+
+# --------------------------------------------------------------------------
+# Gradient descent baseline (Sec. V-A) and the device generator's definition
+# --------------------------------------------------------------------------
+
+def test_gradient_of_R_matches_finite_differences():
+    inst = synth.make_instance(30, 5, 1e-1, seed=29, grid=2)
+    G = O.kernel_matrix(inst.Q, inst.scale)
+    rng = np.random.default_rng(4)
+    a = rng.normal(size=30)
+    g = O.gradient_R(G, a, inst.y, inst.lam)
+    h = 1e-5
+    for _ in range(5):
+        v = rng.normal(size=30)
+        fd = (O.objective_R(G, a + h * v, inst.y, inst.lam) - O.objective_R(G, a - h * v, inst.y, inst.lam)) / (2 * h)
+        assert abs(fd - g @ v) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_gradient_descent_contracts_each_eigencomponent_in_closed_form():
+    """With G = V diag(g) V^T, A = G + lambda I and alpha* = A^-1 y, one GD step
+    maps the error e = alpha - alpha* to (I - 2 eta G A) e, so after k steps
+    from alpha^0 = 0 its component along v_i is (1 - 2 eta g_i (g_i + lambda))^k
+    times that of -alpha*."""
+    rng = np.random.default_rng(8)
+    V, _ = np.linalg.qr(rng.normal(size=(9, 9)))
+    g = np.array([3.0, 1.5, 1.0, 0.5, 0.25, 0.1, 0.05, 0.01, 0.0])
+    G = (V * g) @ V.T
+    G = 0.5 * (G + G.T)
+    lam = 0.2
+    y = rng.normal(size=9)
+    a_star = V @ ((V.T @ y) / (g + lam))
+    eta = 0.9 / (2 * g[0] * (g[0] + lam))
+    k = 7
+    res = O.gradient_descent(G, y, lam, eta, max_iter=k)
+    want = a_star + V @ (((1 - 2 * eta * g * (g + lam)) ** k) * (V.T @ -a_star))
+    assert res.steps == k and not res.converged
+    np.testing.assert_allclose(res.alpha, want, rtol=0, atol=1e-12 * np.linalg.norm(a_star))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(res.R, res.R[1:]))   # eta < 1/L: R decreases
+
+
+def test_philox4x32_10_known_answers():
+    from oracle import philox as X
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.json")) as f:
+        kat = json.load(f)
+    for case in kat["cases"]:
+        c = [int(v, 16) for v in case["counter"]]
+        k = [int(v, 16) for v in case["key"]]
+        got = [int(v) for v in X.philox4x32_10(c, k)]
+        assert got == [int(v, 16) for v in case["out"]]
+
+
+def test_philox_gaussian_directions_are_standard_normal():
+    """Moments and tail fractions of 2^18 draws: mean 0, variance 1, fourth
+    moment 3, and the one- and two-sigma fractions of N(0, 1) (0.6827, 0.9545)
+    within five standard errors; the layout is reproducible and row-major."""
+    from oracle import philox as X
+    Z = X.gaussian_directions(1234, 512, 512)
+    z = Z.ravel()
+    m = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(m)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / m)
+    assert abs(np.mean(z ** 4) - 3.0) < 5 * math.sqrt(96.0 / m)
+    for s, p in ((1.0, 0.682689492), (2.0, 0.954499736)):
+        frac = np.mean(np.abs(z) < s)
+        assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / m)
+    np.testing.assert_array_equal(X.gaussian_directions(1234, 3, 5), Z.ravel()[:15].reshape(3, 5))
+    assert not np.array_equal(X.gaussian_directions(1235, 3, 5), Z.ravel()[:15].reshape(3, 5))
