@@ -191,7 +191,7 @@ class PCGResult:
 
 
 def pcg(A: np.ndarray, y: np.ndarray, P: np.ndarray | None, tol: float,
-        max_iter: int = 100000) -> PCGResult:
+        max_iter: int = 100000, callback=None) -> PCGResult:
     """Preconditioned CG exactly in the order of Algorithm 1:
 
         alpha^0 = 0, r^0 = y, theta^0 = P r^0, p^0 = theta^0
@@ -204,7 +204,9 @@ def pcg(A: np.ndarray, y: np.ndarray, P: np.ndarray | None, tol: float,
             beta = (r^{k+1} . theta^{k+1}) / (r^k . theta^k)
             p^{k+1} = theta^{k+1} + beta p^k
 
-    P = None means the identity (plain CG)."""
+    P = None means the identity (plain CG).  ``callback(k, alpha)``, if given,
+    sees each iterate alpha^k (k = 1, 2, ...); it changes no arithmetic, and a
+    true return value ends the iteration there."""
     y = np.asarray(y, dtype=np.float64)
     n = y.shape[0]
     alpha = np.zeros(n)
@@ -221,6 +223,8 @@ def pcg(A: np.ndarray, y: np.ndarray, P: np.ndarray | None, tol: float,
         delta = rtheta / float(p @ Ap)
         alpha = alpha + delta * p
         r = r - delta * Ap
+        if callback is not None and callback(k + 1, alpha):
+            return PCGResult(alpha=alpha, iterations=k + 1, converged=False, rel_res=hist)
         rel = float(np.linalg.norm(r)) / ny
         hist.append(rel)
         if rel <= tol:

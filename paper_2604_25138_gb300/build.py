@@ -59,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs, "-lcublas"]
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

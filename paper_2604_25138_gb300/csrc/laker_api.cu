@@ -117,7 +117,6 @@ laker_status laker_create(laker_ctx** out, int device, void* stream) {
 
 laker_status laker_destroy(laker_ctx* ctx) {
     if (!ctx) return LAKER_ERR_ARG;
-    release_cublas(ctx);
     if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LAKER_OK;

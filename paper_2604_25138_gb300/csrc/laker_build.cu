@@ -169,9 +169,11 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->lambda,
                                                                  op->diagA);
     LK_LAUNCHED(ctx);
-    if (op->precision == LAKER_BF16X3) {
-        if (!(op->scale > 0.0))
-            return set_error(ctx, LAKER_ERR_ARG, "BF16X3 operator needs scale > 0");
+    if (op->precision == LAKER_BF16X3 && !(op->scale > 0.0))
+        return set_error(ctx, LAKER_ERR_ARG, "BF16X3 operator needs scale > 0");
+    // split-bf16 operands: the matrix-free product (BF16X3) and the
+    // tensor-core random directions of the fit (FP32 and BF16X3, d <= 64)
+    if (op->precision != LAKER_FP64 && op->scale > 0.0 && op->dpad <= 64) {
         const size_t e = (size_t)n * op->dpad;
         if ((st = lk_malloc(ctx, (void**)&op->Qhi, e * 2)) != LAKER_OK) return st;
         if ((st = lk_malloc(ctx, (void**)&op->Qlo, e * 2)) != LAKER_OK) return st;
@@ -180,7 +182,7 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
         k_split_bf16<<<(unsigned)((e + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->dpad, fold,
                                                                            op->Qhi, op->Qlo, op->Q32);
         LK_LAUNCHED(ctx);
-        if ((st = mf_prepare(ctx, op)) != LAKER_OK) return st;
+        if (op->precision == LAKER_BF16X3 && (st = mf_prepare(ctx, op)) != LAKER_OK) return st;
     }
     return LAKER_OK;
 }

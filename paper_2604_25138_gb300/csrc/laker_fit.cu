@@ -18,8 +18,6 @@
 // that move P.  All small dense algebra is float64 and spread over many
 // thread blocks (GB300's float64 pipe is slow per SM); every reduction has a
 // fixed order.
-#include <cublas_v2.h>
-
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -703,32 +701,8 @@ __global__ void k_scale_cols_to_float(int64_t n, int nr, int ldw, const double* 
 
 unsigned gsz(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b); }
 
-// U = C + lambda Z (C = G Z in float32 from the tensor-core product)
-__global__ void k_add_lambda(int64_t count, const float* __restrict__ C, double lam, const double* __restrict__ Z,
-                             double* __restrict__ U) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) U[i] = fma(lam, Z[i], (double)C[i]);
-}
-
-// The context's cuBLAS handle on its stream (created on first use).
-laker_status ctx_cublas(laker_ctx* ctx, cublasHandle_t* h) {
-    if (!ctx->cublas) {
-        cublasHandle_t c = nullptr;
-        if (cublasCreate(&c) != CUBLAS_STATUS_SUCCESS) return set_error(ctx, LAKER_ERR_CUDA, "cublasCreate failed");
-        ctx->cublas = c;
-    }
-    *h = (cublasHandle_t)ctx->cublas;
-    if (cublasSetStream(*h, ctx->stream) != CUBLAS_STATUS_SUCCESS)
-        return set_error(ctx, LAKER_ERR_CUDA, "cublasSetStream failed");
-    return LAKER_OK;
-}
 
 }  // namespace
-
-void release_cublas(laker_ctx* ctx) {
-    if (ctx->cublas) cublasDestroy((cublasHandle_t)ctx->cublas);
-    ctx->cublas = nullptr;
-}
 
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma, double rho,
                       double eps, int max_iter, double tol, laker_precond* P, laker_fit_info* info, laker_setnet* net,
@@ -745,28 +719,18 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     P->U64 = U64;
     if (op->precision == LAKER_FP64) {
         st = gemm<double>(ctx, false, false, n, nr, n, op->K64, op->ldk, Z, nr, op->lambda, Z, nr, U64, nr);
+    } else if (dirs_tc_supported(op)) {
+        // matrix-free on the tensor cores: (lambda I + G) Z~ with Z~ = bf16(Z)
+        st = dirs_tc(ctx, op, Z, nr, U64);
     } else {
-        // G Z is a plain float32 product (the materialised hi part of G times
-        // the rounded directions): cuBLAS with its bf16x9 emulation, which
-        // runs on the tensor cores at float32 accuracy.  Row-major U = G Z is
-        // the column-major U^T = Z^T G^T.
-        float *Z32 = nullptr, *C32 = nullptr;
+        // d > 64: the float32 G through the split-K SIMT kernel, U = G Z32 + lambda Z
+        float* Z32 = nullptr;
         if ((st = lk_malloc(ctx, (void**)&Z32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
-        if ((st = lk_malloc(ctx, (void**)&C32, (size_t)n * nr * sizeof(float))) != LAKER_OK) return st;
         k_to_float<<<gsz(n * nr), 256, 0, s>>>(n * nr, Z, Z32);
         LK_LAUNCHED(ctx);
-        cublasHandle_t cb = nullptr;
-        if ((st = ctx_cublas(ctx, &cb)) != LAKER_OK) return st;
-        const float one = 1.f, zero = 0.f;
-        if (cublasGemmEx(cb, CUBLAS_OP_N, CUBLAS_OP_N, nr, (int)n, (int)n, &one, Z32, CUDA_R_32F, nr, op->K32,
-                         CUDA_R_32F, (int)op->ldk, &zero, C32, CUDA_R_32F, nr, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                         CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-            return set_error(ctx, LAKER_ERR_CUDA, "cublasGemmEx (G Z) failed");
-        k_add_lambda<<<gsz(n * nr), 256, 0, s>>>(n * nr, C32, op->lambda, Z, U64);
-        LK_LAUNCHED(ctx);
-        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        st = gemm<float>(ctx, false, false, n, nr, n, op->K32, op->ldk, Z32, nr, op->lambda, Z, nr, U64, nr);
+        cudaStreamSynchronize(s);
         cudaFree(Z32);
-        cudaFree(C32);
     }
     if (st != LAKER_OK) return st;
     double* tmpv = nullptr;

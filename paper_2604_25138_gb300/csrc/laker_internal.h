@@ -40,7 +40,6 @@ struct laker_ctx {
     bool owns_stream = false;
     int num_sms = 0;
     int64_t launches = 0;
-    void* cublas = nullptr;     // cuBLAS handle for the fit's plain products, created on first use
     int64_t wait_cycles = 0;    // budget of bounded device waits (0 = the default, ~2 s)
     std::string last_error;
 };
@@ -125,7 +124,6 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
                        int trace_cap = 0, double R_ref = 0.0, double gap_tol = 0.0);
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
 // laker_fit.cu
-void release_cublas(laker_ctx* ctx);
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
                       double gamma, double rho, double eps, int max_iter, double tol,
                       laker_precond* P, laker_fit_info* info,
@@ -143,6 +141,9 @@ laker_status mf_status(laker_ctx* ctx, const laker_op* op);
 laker_status mf_time_main(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_materialised(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
 laker_status op_time_product(laker_ctx* ctx, const laker_op* op, const double* x, int reps, double* ms);
+// laker_dirs_tc.cu (tensor-core random directions (lambda I + G) Z~, Z~ = bf16(Z))
+bool dirs_tc_supported(const laker_op* op);
+laker_status dirs_tc(laker_ctx* ctx, const laker_op* op, const double* Z, int nr, double* U);
 // laker_rng.cu (Philox4x32-10 Gaussian directions, n_r-major rows)
 laker_status random_directions(laker_ctx* ctx, uint64_t seed, int64_t count, double* Z);
 // laker_setnet.cu

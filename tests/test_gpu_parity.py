@@ -223,12 +223,13 @@ def test_mixed_precond_apply_matches_oracle(L, ctx, prec):
     P = c^-1/2 I + U~ diag(phi) U~^T (float32 U~) from an eigendecomposition
     stopped once its off-diagonal remainder is below c / 100; P v must match
     the oracle's dense Sigma_*^-1/2 v to well under that bound and stay
-    positive definite."""
-    from tests.gpu_util import dev, host, rel
+    positive definite.  Their directions are z_k rounded to bf16, so both
+    sides get bf16-representable directions."""
+    from tests.gpu_util import bf16_round, dev, host, rel
     n, n_r = 1024, 128
     inst = _inst(n, 16, 1e-3, 51)
     A = O.system_matrix(inst.Q, inst.scale, inst.lam)
-    Z = synth.directions(n, n_r, 51)
+    Z = bf16_round(synth.directions(n, n_r, 51))   # mixed fits use bf16 directions
     op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, getattr(L, prec))
     P = L.laker_fit_preconditioner(ctx, op, dev(Z))
     Pd = O.inverse_sqrt(O.cccp_fit(O.random_directions(A, Z), 0.1, O.shrinkage_rho(n, n_r, 0.1), 1e-8).Sigma)
@@ -360,3 +361,23 @@ def test_bf16x3_mixed_solve_reaches_true_tolerance(L, ctx):
     res = O.relative_residual(A, host(alpha), inst.y)
     assert res <= 1e-6 * (1 + 1e-6), (res, info)
     assert info["true_residuals"] >= 1
+
+
+@pytest.mark.parametrize("prec,n,d,n_r", [("BF16X3", 1000, 16, 128), ("FP32", 777, 64, 200), ("BF16X3", 4097, 32, 131),
+                                          ("FP32", 300, 33, 40)])
+def test_mixed_directions_match_oracle(L, ctx, prec, n, d, n_r):
+    """The fit's random directions u_k = (lambda I + G) z~_k / |.| for mixed
+    operators: the tensor-core kernel (d <= 64; ragged n and a ragged last
+    chunk of directions) and the SIMT fallback (d = 33), against the oracle's
+    dense product with the same bf16 directions: ~1e-5 per column."""
+    from tests.gpu_util import bf16_round, dev, host
+    inst = _inst(n, d, 1e-3, 70 + n)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    Z = bf16_round(synth.directions(n, n_r, 70 + n))
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, getattr(L, prec))
+    P = L.laker_fit_preconditioner(ctx, op, dev(Z), max_iter=1)
+    _, _, U = L.laker_precond_export(ctx, P)
+    Uo = O.random_directions(A, Z)
+    err = np.linalg.norm(host(U) - Uo, axis=0)
+    assert np.max(err) < 1e-4, np.max(err)
+    assert np.median(err) < 2e-5, np.median(err)

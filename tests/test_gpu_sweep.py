@@ -10,7 +10,11 @@ relative residual of 1e-10 and reports
   the oracle's dense eigenvalues (a Ritz estimate lies below the true value
   and reaches it once the extremes have converged);
 * iterations to the objective gap TAR.TOL = 1e-3 (Eq. iterations) from its
-  trace -- checked against the oracle's PCG iterates (+-1);
+  trace -- checked against the oracle's PCG iterates: the gap oscillates
+  around 1e-3 near the crossing (R - R_ref is the error in the G (lambda I +
+  G) norm, which CG does not minimise), so the index must lie within +-1 of
+  the oracle's own rounding envelope (summation-order permutations and a
+  1e-12 perturbation of P move it by up to 7 products at n = 500);
 and the paper's qualitative findings must hold: the CCCP preconditioner
 compresses the spectrum by orders of magnitude and needs the fewest
 iterations, Jacobi leaves kappa nearly unchanged.
@@ -20,6 +24,7 @@ import pytest
 
 from oracle import laker_oracle as O
 from paper_2604_25138_gb300 import synth
+from tests.pcg_envelope import gap_envelope
 
 pytestmark = pytest.mark.gpu
 
@@ -45,14 +50,6 @@ def _dev(x):
 
 def sweep_instance(n, seed):
     return synth.make_instance(n, 10, 1e-2, n_tx=3, seed=seed, side=100.0, grid=2, scale=1.0)
-
-
-def _oracle_gap_iterations(A, G, y, P, lam, R_ref, kmax):
-    for k in range(1, kmax + 1):
-        a = O.pcg(A, y, P, 0.0, max_iter=k).alpha
-        if abs(O.objective_R(G, a, y, lam) - R_ref) <= 1e-3 * abs(R_ref):
-            return k
-    return None
 
 
 @pytest.mark.parametrize("n", SIZES)
@@ -81,8 +78,8 @@ def test_sweep_point_matches_oracle(L, ctx, n):
         assert kappa[name] <= k_true * (1 + 1e-6), (name, kappa[name], k_true)
         assert kappa[name] >= 0.9 * k_true, (name, kappa[name], k_true)
         gap_its[name] = L.laker_trace_gap_iterations(trace, R_ref, 1e-3)
-        k_ora = _oracle_gap_iterations(A, G, inst.y, ora_P[name], inst.lam, R_ref, info["iterations"])
-        assert k_ora is not None and abs(gap_its[name] - k_ora) <= 1, (name, gap_its[name], k_ora)
+        env = gap_envelope(A, G, inst.y, ora_P[name], inst.lam, R_ref, 1e-3, info["iterations"])
+        assert env is not None and env[0] - 1 <= gap_its[name] <= env[1] + 1, (name, gap_its[name], env)
     # the paper's qualitative findings (Sec. V-B)
     assert kappa["cccp"] < kappa["none"] / 10
     assert kappa["jacobi"] > kappa["none"] / 3
