@@ -369,7 +369,12 @@ def test_mixed_directions_match_oracle(L, ctx, prec, n, d, n_r):
     """The fit's random directions u_k = (lambda I + G) z~_k / |.| for mixed
     operators: the tensor-core kernel (d <= 64; ragged n and a ragged last
     chunk of directions) and the SIMT fallback (d = 33), against the oracle's
-    dense product with the same bf16 directions: ~1e-5 per column."""
+    dense product with the same bf16 directions.  The kernel keeps each
+    element of P = G_IJ in [1/2, 2) as bf16 hi + lo, ~2^-18 absolute, so the
+    error of A z~_k grows like 2^-18 sqrt(n) |z~_k| (rounding errors of
+    random sign), and relative to |A z~_k| it is largest for directions with a
+    small component along A's dominant eigenvector: each column must be within
+    8 times that bound, and the median column within 2e-5."""
     from tests.gpu_util import bf16_round, dev, host
     inst = _inst(n, d, 1e-3, 70 + n)
     A = O.system_matrix(inst.Q, inst.scale, inst.lam)
@@ -379,5 +384,6 @@ def test_mixed_directions_match_oracle(L, ctx, prec, n, d, n_r):
     _, _, U = L.laker_precond_export(ctx, P)
     Uo = O.random_directions(A, Z)
     err = np.linalg.norm(host(U) - Uo, axis=0)
-    assert np.max(err) < 1e-4, np.max(err)
+    bound = 8 * 2.0 ** -18 * np.sqrt(n) * np.linalg.norm(Z, axis=0) / np.linalg.norm(A @ Z, axis=0)
+    assert np.all(err <= bound + 1e-9), np.max(err / bound)
     assert np.median(err) < 2e-5, np.median(err)
