@@ -145,16 +145,18 @@ __device__ __forceinline__ void mf_lane_reduce(float* a, int lane) {
     }
 }
 
+// Both 16-column loads are issued before one wait, so a tile exposes one
+// tensor-memory read latency.
 template <bool DIAG>
 __device__ __forceinline__ void mf_tile_epilogue(uint32_t tcol, float2* acc, const float4* pI4, float pj, float2* sJ) {
     static_assert(MF_WCOLS == 32, "two 16-column chunks per warp");
-    uint32_t v[16];
+    uint32_t v[32];
     tmem_ld16(tcol, v);
+    tmem_ld16(tcol + 16, v + 16);
     tmem_wait(v);
+    tmem_wait(v + 16);
     mf_chunk<DIAG>(v, acc, pI4, pj, sJ);
-    tmem_ld16(tcol + 16, v);
-    tmem_wait(v);
-    mf_chunk<DIAG>(v, acc + 8, pI4 + 4, pj, sJ);
+    mf_chunk<DIAG>(v + 16, acc + 8, pI4 + 4, pj, sJ);
 }
 
 // Tile (I, J): logits D[j][i] = q'_j . q'_i for the 128 j of block J
@@ -250,6 +252,11 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = instr_desc_bf16(MF_B, MF_B);
+            // shared-memory descriptors built once: the start-address field is
+            // the byte address / 16, so tile q of the ring is dA0 + q TILE / 16
+            // and the K step kk (32 bytes) adds 2 (all addresses < 256 KB)
+            const uint64_t dA0 = smem_desc(sA, C::SWZ, 0);
+            const uint64_t dBh = smem_desc(sB_hi, C::SWZ, 0), dBl = smem_desc(sB_lo, C::SWZ, 0);
             int seg = 0, I = I0, k = k0;
             for (int it = 0; it < ntiles; ++it) {
                 if (it == 0 || k == 0) {
@@ -265,16 +272,15 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
                 tc_fence_after();
                 if (!mbar_wait(&S->full[st], ph, err)) break;
                 tc_fence_after();
-                const unsigned char* ah = sA + 2 * st * TILE;
-                const unsigned char* al = ah + TILE;
+                const uint64_t dAh = dA0 + (uint64_t)((2 * st * TILE) >> 4), dAl = dAh + (uint64_t)(TILE >> 4);
                 const uint32_t d = tmem + acc * MF_B;
 #pragma unroll
                 for (int kk = 0; kk < DPAD / 16; ++kk) {
-                    const int kb = kk * 32;   // 16 bf16 = 32 bytes along K
-                    umma_bf16(d, smem_desc(ah, C::SWZ, kb), smem_desc(sB_hi, C::SWZ, kb), idesc, kk > 0 ? 1u : 0u);
-                    umma_bf16(d, smem_desc(ah, C::SWZ, kb), smem_desc(sB_lo, C::SWZ, kb), idesc, 1u);
-                    umma_bf16(d, smem_desc(al, C::SWZ, kb), smem_desc(sB_hi, C::SWZ, kb), idesc, 1u);
-                    umma_bf16(d, smem_desc(al, C::SWZ, kb), smem_desc(sB_lo, C::SWZ, kb), idesc, 1u);
+                    const uint64_t o = 2 * kk;   // 16 bf16 = 32 bytes along K
+                    umma_bf16(d, dAh + o, dBh + o, idesc, kk > 0 ? 1u : 0u);
+                    umma_bf16(d, dAh + o, dBl + o, idesc, 1u);
+                    umma_bf16(d, dAl + o, dBh + o, idesc, 1u);
+                    umma_bf16(d, dAl + o, dBl + o, idesc, 1u);
                 }
                 umma_commit(&S->empty[st]);
                 umma_commit(&S->tfull[acc]);

@@ -117,7 +117,10 @@ def test_gap_stop_matches_oracle(L, ctx, n, lam, prec):
         Pd = O.jacobi_preconditioner(A)
     R_ref = O.objective_R(G, O.solve_direct(A, inst.y), inst.y, inst.lam)
     alpha, info = L.laker_pcg_solve_gap(ctx, op, P, _dev(inst.y), R_ref, gap=1e-3)
-    env = gap_envelope(A, G, inst.y, Pd, inst.lam, R_ref, 1e-3, 2000)
+    v = synth.random_vector(n, 4)
+    pv_err = np.linalg.norm(L.laker_precond_apply(ctx, P, _dev(v)).cpu().numpy() - Pd @ v) / np.linalg.norm(Pd @ v)
+    assert pv_err < 1e-7
+    env = gap_envelope(A, G, inst.y, Pd, inst.lam, R_ref, 1e-3, 2000, p_rel=max(pv_err, 1e-15))
     assert env is not None
     assert info["converged"] == 1 and env[0] - 1 <= info["iterations"] <= env[1] + 1, (info, env)
     assert O.objective_gap(G, alpha.cpu().numpy(), O.solve_direct(A, inst.y), inst.y, inst.lam) <= 1e-3 * (1 + 1e-6)
