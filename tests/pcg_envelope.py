@@ -68,3 +68,10 @@ def gap_envelope(A, G, y, P, lam, R_ref, gap, kmax, n_perm=6, p_rel=1e-9, n_pert
             ks.append(gap_crossing(A, G, y, _NoisyP(P, p_rel, rng), lam, R_ref, gap, kmax))
     ks = [k for k in ks if k is not None]
     return (min(ks), max(ks)) if ks else None
+
+
+def within_envelope(k, env):
+    """k inside the envelope widened by its own width (at least 1): the range
+    of a dozen rounding samples covers only part of the index's spread."""
+    w = max(1, env[1] - env[0])
+    return env[0] - w <= k <= env[1] + w

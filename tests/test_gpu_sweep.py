@@ -18,7 +18,10 @@ relative residual of 1e-10 and reports
   between the GPU's apply and the oracle's dense one (~1e-9 for the float64
   CCCP form c^-1/2 r + U B U^T r, whose B cancels inside the product).  At
   that level two CG runs part after ~30 products (checked product by product
-  at n = 2000), and the index spreads over several products;
+  at n = 2000), and the index spreads over several products.  So the index
+  must be an exact first crossing of the GPU's own iterates (checked by the
+  oracle on them) and lie within the oracle's envelope widened by its own
+  width;
 and the paper's qualitative findings must hold: the CCCP preconditioner
 compresses the spectrum by orders of magnitude and needs the fewest
 iterations, Jacobi leaves kappa nearly unchanged.
@@ -28,7 +31,7 @@ import pytest
 
 from oracle import laker_oracle as O
 from paper_2604_25138_gb300 import synth
-from tests.pcg_envelope import gap_envelope
+from tests.pcg_envelope import gap_envelope, within_envelope
 
 pytestmark = pytest.mark.gpu
 
@@ -104,8 +107,15 @@ def test_sweep_point_matches_oracle(L, ctx, n):
             env2 = gap_envelope(A, G, inst.y, P_gpu_sigma, inst.lam, R_ref, 1e-3, info["iterations"], n_perm=2,
                                 p_rel=noise[name], seed=1)
             env = (min(env[0], env2[0]), max(env[1], env2[1]))
-        assert env is not None and env[0] - 1 <= gap_its[name] <= env[1] + 1, (name, gap_its[name], env, sig_err,
-                                                                               pv_err)
+        assert env is not None and within_envelope(gap_its[name], env), (name, gap_its[name], env, sig_err, pv_err)
+        # and the index is an exact crossing of the GPU's own trajectory: its
+        # iterate after k products is within the gap, the one before is not
+        k = gap_its[name]
+        a_k, _ = L.laker_pcg_solve(ctx, op, gpu_P[name], _dev(inst.y), 0.0, max_iter=k, allow_maxiter=True)
+        assert O.objective_gap(G, a_k.cpu().numpy(), a_star, inst.y, inst.lam) <= 1e-3 * (1 + 1e-9)
+        if k > 1:
+            a_p, _ = L.laker_pcg_solve(ctx, op, gpu_P[name], _dev(inst.y), 0.0, max_iter=k - 1, allow_maxiter=True)
+            assert O.objective_gap(G, a_p.cpu().numpy(), a_star, inst.y, inst.lam) > 1e-3 * (1 - 1e-9)
     # the paper's qualitative findings (Sec. V-B)
     assert kappa["cccp"] < kappa["none"] / 10
     assert kappa["jacobi"] > kappa["none"] / 3
