@@ -39,6 +39,7 @@ laker_status check_ctx(laker_ctx* ctx) {
 void free_op(laker_op* op) {
     if (!op) return;
     mf_release(op);
+    resid_release(op);
     cudaFree(op->Q64);
     cudaFree(op->Qhi);
     cudaFree(op->Qlo);

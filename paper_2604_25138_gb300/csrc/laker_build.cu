@@ -19,10 +19,20 @@ namespace {
 constexpr int BT = 64;   // output tile edge
 constexpr int BD = 32;   // embedding-dimension chunk
 
-template <bool PAIR>
+// Position of the 128 x 128 tile (I, J), I <= J, of the packed upper triangle
+// of nb blocks (row-major over I).
+__device__ __forceinline__ int64_t pk_tile(int I, int J, int nb) {
+    return (int64_t)I * nb - (int64_t)I * (I - 1) / 2 + (J - I);
+}
+
+// MODE 0: float64 G, full n x ldk; MODE 1: float32 pair (hi, lo), full; MODE 2:
+// float32 pair in the packed upper triangle of 128 x 128 tiles (K32 is the
+// packed array; ldk is the number of 128-blocks), padding entries zero.
+template <int MODE>
 __global__ void __launch_bounds__(256)
 k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
             double* __restrict__ K64, float* __restrict__ K32, float* __restrict__ K32lo, int64_t ldk, int nt) {
+    constexpr bool PAIR = MODE != 0;
     // blockIdx.x enumerates the upper-triangular tile pairs row by row.
     int64_t t = blockIdx.x;
     int bi = 0;
@@ -74,7 +84,14 @@ k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
             const int64_t j = (int64_t)bj * BT + c;
             const double g = exp(scale * acc[u][v]);
             T[r][c] = g;
-            if (i < n && j < n) {
+            if (MODE == 2) {
+                const double gz = (i < n && j < n) ? g : 0.0;
+                const float h = (float)gz;
+                float* tile = K32 + pk_tile(bi >> 1, bj >> 1, (int)ldk) * (2 * 128 * 128);
+                const int row = (bi & 1) * BT + r, col = (bj & 1) * BT + c;
+                tile[row * 128 + col] = h;
+                tile[128 * 128 + row * 128 + col] = (float)(gz - (double)h);
+            } else if (i < n && j < n) {
                 if (PAIR) {
                     const float h = (float)g;
                     K32[i * ldk + j] = h;
@@ -86,11 +103,19 @@ k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
         }
     }
     if (bi == bj) return;
+    // packed: only a diagonal 128-tile needs its lower 64 x 64 block mirrored
+    if (MODE == 2 && (bi >> 1) != (bj >> 1)) return;
     __syncthreads();
     for (int idx = threadIdx.x; idx < BT * BT; idx += blockDim.x) {
         const int c = idx / BT, r = idx % BT;   // output row bj*BT + c, column bi*BT + r
         const int64_t oi = (int64_t)bj * BT + c, oj = (int64_t)bi * BT + r;
-        if (oi < n && oj < n) {
+        if (MODE == 2) {
+            const double gz = (oi < n && oj < n) ? T[r][c] : 0.0;
+            const float h = (float)gz;
+            float* tile = K32 + pk_tile(bi >> 1, bj >> 1, (int)ldk) * (2 * 128 * 128);
+            tile[(BT + c) * 128 + r] = h;
+            tile[128 * 128 + (BT + c) * 128 + r] = (float)(gz - (double)h);
+        } else if (oi < n && oj < n) {
             const double g = T[r][c];
             if (PAIR) {
                 const float h = (float)g;
@@ -137,17 +162,23 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
     const int d = op->d;
     op->ldk = (n + 3) / 4 * 4;
     op->dpad = (d + 15) / 16 * 16;
-    const bool pair = (op->precision != LAKER_FP64);
+    // FP64: float64 G; FP32: the float32 pair, full (its float32 product
+    // streams rows of hi); BF16X3: the pair packed in the upper triangle, read
+    // only by the float64-accurate product (the operator is matrix-free)
+    const int mode = op->precision == LAKER_FP64 ? 0 : op->precision == LAKER_FP32 ? 1 : 2;
     laker_status st;
-    if (pair) {
+    float* Kp = nullptr;
+    if (mode == 1) {
         if ((st = lk_malloc(ctx, (void**)&op->K32, (size_t)n * op->ldk * sizeof(float))) != LAKER_OK) return st;
         if ((st = lk_malloc(ctx, (void**)&op->K32lo, (size_t)n * op->ldk * sizeof(float))) != LAKER_OK) return st;
-    } else {
+    } else if (mode == 0) {
         if ((st = lk_malloc(ctx, (void**)&op->K64, (size_t)n * op->ldk * sizeof(double))) != LAKER_OK) return st;
+    } else {
+        if ((st = resid_prepare(ctx, op, &Kp)) != LAKER_OK) return st;
     }
     if ((st = lk_malloc(ctx, (void**)&op->diagA, (size_t)n * sizeof(double))) != LAKER_OK) return st;
-    if (op->ldk > n) {
-        if (pair) {
+    if (op->ldk > n && mode != 2) {
+        if (mode == 1) {
             LK_CUDA(ctx, cudaMemset2DAsync(op->K32 + n, op->ldk * sizeof(float), 0, (op->ldk - n) * sizeof(float), n,
                                            ctx->stream));
             LK_CUDA(ctx, cudaMemset2DAsync(op->K32lo + n, op->ldk * sizeof(float), 0, (op->ldk - n) * sizeof(float),
@@ -157,14 +188,22 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
                                            ctx->stream));
         }
     }
-    const int nt = (int)((n + BT - 1) / BT);
-    const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
-    if (pair)
-        k_build_sym<true><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, op->K32,
-                                                                    op->K32lo, op->ldk, nt);
-    else
-        k_build_sym<false><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64, nullptr,
+    if (mode == 2) {
+        const int nb128 = (int)((n + 127) / 128);
+        const int nt = 2 * nb128;   // 64-blocks, padded so that every packed tile is written
+        const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
+        k_build_sym<2><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, Kp, nullptr,
+                                                                 nb128, nt);
+    } else {
+        const int nt = (int)((n + BT - 1) / BT);
+        const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
+        if (mode == 1)
+            k_build_sym<1><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, op->K32,
+                                                                     op->K32lo, op->ldk, nt);
+        else
+            k_build_sym<0><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64, nullptr,
                                                                      nullptr, op->ldk, nt);
+    }
     LK_LAUNCHED(ctx);
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->lambda,
                                                                  op->diagA);

@@ -63,6 +63,7 @@ struct laker_op {
     float* K32lo = nullptr;   // n x ldk, G - K32 rounded to float: K32 + K32lo is G to ~2^-48
     double* diagA = nullptr;  // n, lambda + G_ii
     void* mf = nullptr;       // matrix-free operator workspace (tensor maps, buffers)
+    void* rw = nullptr;       // packed float32 pair and schedule of the float64-accurate product (BF16X3)
 };
 
 // Largest number of random directions N_r (a preconditioner apply keeps the
@@ -144,6 +145,11 @@ laker_status op_time_product(laker_ctx* ctx, const laker_op* op, const double* x
 // laker_dirs_tc.cu (tensor-core random directions (lambda I + G) Z~, Z~ = bf16(Z))
 bool dirs_tc_supported(const laker_op* op);
 laker_status dirs_tc(laker_ctx* ctx, const laker_op* op, const double* Z, int nr, double* U);
+// laker_resid.cu (float64-accurate product from the packed upper-triangular pair)
+laker_status resid_prepare(laker_ctx* ctx, laker_op* op, float** Kp);
+void resid_release(laker_op* op);
+laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w, const PcgScalars* sc,
+                          int gate);
 // laker_rng.cu (Philox4x32-10 Gaussian directions, n_r-major rows)
 laker_status random_directions(laker_ctx* ctx, uint64_t seed, int64_t count, double* Z);
 // laker_setnet.cu

@@ -768,7 +768,9 @@ laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecVie
     LK_LAUNCHED(ctx);
     if (mixed) {
         // TR1: w2 = (lambda I + G) alpha in double-float, only when a true residual is due
-        if ((st = launch_mv_df(ctx, op, alpha, ws.w2, ws.sc, GATE_TRUE, ws.mv_blocks)) != LAKER_OK) return st;
+        st = op->rw ? resid_matvec(ctx, op, alpha, ws.w2, ws.sc, 1)
+                    : launch_mv_df(ctx, op, alpha, ws.w2, ws.sc, GATE_TRUE, ws.mv_blocks);
+        if (st != LAKER_OK) return st;
         k_true_residual<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.r, ws.sc, ws.partials);
         LK_LAUNCHED(ctx);
     }
@@ -794,6 +796,7 @@ laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x
 }
 
 laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
+    if (op->rw) return resid_matvec(ctx, op, x, w, nullptr, 0);
     if (op->precision != LAKER_FP64) return launch_mv_df(ctx, op, x, w, nullptr, GATE_NONE, mv_blocks_for(ctx, op->n));
     return launch_mv<double>(ctx, op, op->K64, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
                              mv_blocks_for(ctx, op->n));

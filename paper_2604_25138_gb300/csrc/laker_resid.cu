@@ -1,0 +1,248 @@
+// Float64-accurate product w = (lambda I + G) x for split-bf16 operators, the
+// true residual of mixed-precision PCG (residual replacement every k
+// products; Sec. IV-E PCG with reliable updates).
+//
+// Near convergence the terms G_ij alpha_j are ~1e4 and cancel to O(1) sums, so
+// each kernel value must be right to ~2^-45: it is stored, once per unordered
+// pair, as a float32 pair (hi, lo) with hi + lo = G_ij to ~2^-48.  G is
+// symmetric, so only the upper triangle of 128 x 128 tiles is kept, tile
+// (I, J), I <= J, at position I nb - I (I - 1)/2 + (J - I) of a packed array,
+// hi tile then lo tile, row-major: half the bytes of the full pair, and each
+// stored value serves both its row sum (sum_j G_ij x_j, i in block I) and,
+// off the diagonal, its column sum (sum_i G_ij x_i, j in block J).
+//
+// k_df_sym: one CTA per SM on a contiguous range of the tiles (row-major over
+// I); 16 warps, warp w takes rows 8w .. 8w + 7 of a tile and lane l the
+// columns 4l .. 4l + 3 (16-byte streaming loads, all eight rows' loads issued
+// before the arithmetic).  Products are accumulated with the K = 3 dot product
+// of Ogita, Rump and Oishi (Dot3 in laker_df.cuh) in float32 arithmetic:
+// rows in registers for the CTA's whole segment of block row I, columns per
+// tile (reduced over the 16 warps in shared memory in a fixed order).
+// k_df_sym_finish adds lambda x_i, the row partials of the segments of block
+// I and the column partials of the tiles (I', I), I' < I, in a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "laker_device.cuh"
+#include "laker_df.cuh"
+
+namespace {
+
+constexpr int RT = 128;              // tile edge
+constexpr int RW = 16;               // warps per CTA
+constexpr int RR = RT / RW;          // rows per warp
+
+struct RSched {
+    int nb;        // blocks of 128
+    int64_t T;     // tiles nb (nb + 1) / 2
+    int G;         // CTAs
+    int slots;     // max CTAs sharing one block row
+};
+
+__host__ __device__ __forceinline__ int64_t r_row_start(int I, int nb) {
+    return (int64_t)I * nb - (int64_t)I * (I - 1) / 2;
+}
+__host__ __device__ __forceinline__ int64_t r_begin(int64_t g, const RSched& s) { return g * s.T / s.G; }
+__host__ __device__ __forceinline__ int r_owner(int64_t t, const RSched& s) {
+    int g = (int)((t * s.G) / s.T);
+    while (g + 1 < s.G && r_begin(g + 1, s) <= t) ++g;
+    while (g > 0 && r_begin(g, s) > t) --g;
+    return g;
+}
+__host__ __device__ __forceinline__ int r_row_of(int64_t t, int nb) {
+    int I = 0;
+    while (I + 1 < nb && r_row_start(I + 1, nb) <= t) ++I;
+    return I;
+}
+
+__device__ __forceinline__ bool r_gated(const PcgScalars* sc, int gate) {
+    if (sc == nullptr || gate == 0) return false;
+    if (*(volatile const int*)&sc->converged != 0) return true;
+    return *(volatile const int*)&sc->need_true == 0;
+}
+
+__device__ __forceinline__ lk::df2 shfl_df(lk::df2 v, int o) {
+    lk::df2 u;
+    u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    return u;
+}
+
+__global__ void __launch_bounds__(RW * 32, 1)
+k_df_sym(const float* __restrict__ Kp, RSched sch, int64_t n, const double* __restrict__ x,
+         float2* __restrict__ rowpart, float2* __restrict__ colpart, const PcgScalars* sc, int gate) {
+    if (r_gated(sc, gate)) return;
+    __shared__ float2 xI[RT], xJ[RT];
+    __shared__ float2 cred[RW][RT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x;
+    const int64_t t0 = r_begin(g, sch), t1 = r_begin(g + 1, sch);
+    if (t0 >= t1) return;
+    int I = r_row_of(t0, sch.nb);
+    int J = I + (int)(t0 - r_row_start(I, sch.nb));
+    lk::Dot3 row[RR];
+    auto load_x = [&](float2* dst, int blk) {
+        if (threadIdx.x < RT) {
+            const int64_t i = (int64_t)blk * RT + threadIdx.x;
+            const lk::df2 v = lk::df_from(i < n ? x[i] : 0.0);
+            dst[threadIdx.x] = make_float2(v.hi, v.lo);
+        }
+    };
+    auto flush = [&](int blk) {
+        const int slot = g - r_owner(r_row_start(blk, sch.nb), sch);
+#pragma unroll
+        for (int k = 0; k < RR; ++k) {
+            lk::df2 v = row[k].value();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = lk::df_add(v, shfl_df(v, o));
+            if (lane == 0)
+                rowpart[((int64_t)blk * sch.slots + slot) * RT + warp * RR + k] = make_float2(v.hi, v.lo);
+            row[k] = lk::Dot3();
+        }
+    };
+    load_x(xI, I);
+    bool dirty = false;   // row sums of block I accumulated since the last flush
+    for (int64_t t = t0; t < t1; ++t) {
+        load_x(xJ, J);
+        __syncthreads();
+        const float* hi = Kp + t * (2 * RT * RT);
+        const float* lo = hi + RT * RT;
+        float4 h[RR], l[RR];
+#pragma unroll
+        for (int k = 0; k < RR; ++k) {
+            const int r = warp * RR + k;
+            h[k] = __ldcs(reinterpret_cast<const float4*>(hi + r * RT) + lane);
+            l[k] = __ldcs(reinterpret_cast<const float4*>(lo + r * RT) + lane);
+        }
+        lk::df2 xj[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { const float2 v = xJ[4 * lane + c]; xj[c] = {v.x, v.y}; }
+        const bool diag = (I == J);
+        lk::Dot3 col[4];
+#pragma unroll
+        for (int k = 0; k < RR; ++k) {
+            const float gh[4] = {h[k].x, h[k].y, h[k].z, h[k].w};
+            const float gl[4] = {l[k].x, l[k].y, l[k].z, l[k].w};
+            const float2 xv = xI[warp * RR + k];
+            const lk::df2 xi = {xv.x, xv.y};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const lk::df2 gv = {gh[c], gl[c]};
+                row[k].add(gv, xj[c]);
+                if (!diag) col[c].add(gv, xi);
+            }
+        }
+        dirty = true;
+        if (!diag) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const lk::df2 v = col[c].value();
+                cred[warp][4 * lane + c] = make_float2(v.hi, v.lo);
+            }
+        }
+        __syncthreads();
+        if (!diag && threadIdx.x < RT) {
+            lk::df2 s = {cred[0][threadIdx.x].x, cred[0][threadIdx.x].y};
+#pragma unroll
+            for (int w = 1; w < RW; ++w) s = lk::df_add(s, lk::df2{cred[w][threadIdx.x].x, cred[w][threadIdx.x].y});
+            colpart[t * RT + threadIdx.x] = make_float2(s.hi, s.lo);
+        }
+        // the last tile of block row I: flush this CTA's segment of it
+        if (++J == sch.nb) {
+            flush(I);
+            dirty = false;
+            ++I;
+            J = I;
+            if (t + 1 < t1) load_x(xI, I);   // xI is not read again before the next barrier
+        }
+    }
+    if (dirty) flush(I);
+}
+
+// w_i = lambda x_i + (row partials of block I's segments) + (column partials of
+// the tiles (I', I), I' < I), all in double-float, in a fixed order.
+__global__ void k_df_sym_finish(RSched sch, int64_t n, double lambda, const double* __restrict__ x,
+                                const float2* __restrict__ rowpart, const float2* __restrict__ colpart,
+                                const int* __restrict__ nslots, double* __restrict__ w, const PcgScalars* sc,
+                                int gate) {
+    if (r_gated(sc, gate)) return;
+    const int I = blockIdx.x;
+    const int r = threadIdx.x;
+    const int64_t i = (int64_t)I * RT + r;
+    if (i >= n) return;
+    lk::df2 s = {0.f, 0.f};
+    const int ns = nslots[I];
+    for (int k = 0; k < ns; ++k) {
+        const float2 v = rowpart[((int64_t)I * sch.slots + k) * RT + r];
+        s = lk::df_add(s, lk::df2{v.x, v.y});
+    }
+    for (int Ip = 0; Ip < I; ++Ip) {
+        const float2 v = colpart[(r_row_start(Ip, sch.nb) + (I - Ip)) * RT + r];
+        s = lk::df_add(s, lk::df2{v.x, v.y});
+    }
+    w[i] = fma(lambda, x[i], lk::df_to(s));
+}
+
+}  // namespace
+
+struct ResidWork {
+    RSched sch;
+    float* Kp = nullptr;          // packed (hi, lo) tiles of the upper triangle
+    float2* rowpart = nullptr;
+    float2* colpart = nullptr;
+    int* nslots = nullptr;
+};
+
+void resid_release(laker_op* op) {
+    ResidWork* rw = static_cast<ResidWork*>(op->rw);
+    if (!rw) return;
+    cudaFree(rw->Kp);
+    cudaFree(rw->rowpart);
+    cudaFree(rw->colpart);
+    cudaFree(rw->nslots);
+    delete rw;
+    op->rw = nullptr;
+}
+
+// Packed storage and the tile schedule of an operator (built by the caller).
+laker_status resid_prepare(laker_ctx* ctx, laker_op* op, float** Kp) {
+    ResidWork* rw = new ResidWork();
+    RSched& s = rw->sch;
+    s.nb = (int)((op->n + RT - 1) / RT);
+    s.T = (int64_t)s.nb * (s.nb + 1) / 2;
+    s.G = (int)std::min<int64_t>(s.T, (int64_t)ctx->num_sms);
+    s.slots = 1;
+    std::vector<int> ns((size_t)s.nb);
+    for (int I = 0; I < s.nb; ++I) {
+        const int64_t a = r_row_start(I, s.nb), b = a + (s.nb - I) - 1;
+        ns[(size_t)I] = r_owner(b, s) - r_owner(a, s) + 1;
+        s.slots = std::max(s.slots, ns[(size_t)I]);
+    }
+    op->rw = rw;
+    laker_status st;
+    if ((st = lk_malloc(ctx, (void**)&rw->Kp, (size_t)s.T * 2 * RT * RT * sizeof(float))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&rw->rowpart, (size_t)s.nb * s.slots * RT * sizeof(float2))) != LAKER_OK)
+        return st;
+    if ((st = lk_malloc(ctx, (void**)&rw->colpart, (size_t)s.T * RT * sizeof(float2))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&rw->nslots, (size_t)s.nb * sizeof(int))) != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMemcpyAsync(rw->nslots, ns.data(), sizeof(int) * s.nb, cudaMemcpyHostToDevice, ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *Kp = rw->Kp;
+    return LAKER_OK;
+}
+
+// w = (lambda I + G) x from the packed pair; gate 1 skips the launch's work
+// unless a true residual is due (PCG residual replacement).
+laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w, const PcgScalars* sc,
+                          int gate) {
+    const ResidWork* rw = static_cast<const ResidWork*>(op->rw);
+    if (!rw) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "packed float64-accurate operator not built");
+    k_df_sym<<<(unsigned)rw->sch.G, RW * 32, 0, ctx->stream>>>(rw->Kp, rw->sch, op->n, x, rw->rowpart, rw->colpart,
+                                                                  sc, gate);
+    LK_LAUNCHED(ctx);
+    k_df_sym_finish<<<(unsigned)rw->sch.nb, RT, 0, ctx->stream>>>(rw->sch, op->n, op->lambda, x, rw->rowpart,
+                                                                    rw->colpart, rw->nslots, w, sc, gate);
+    LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}

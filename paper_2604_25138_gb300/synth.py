@@ -151,9 +151,10 @@ def random_vector(n: int, seed: int) -> np.ndarray:
 def default_num_directions(n: int) -> int:
     """The number of random directions N_r.  The paper gives only the shape of
     its schedule (O(sqrt n) for small n, linear for large n, Sec. V-A); this
-    reading takes max(4 sqrt(n), n/16), at most n and 2048: 128 at n = 1024,
-    1024 at n = 16384, 2048 at n = 65536."""
-    return int(min(n, 2048, max(math.ceil(4.0 * math.sqrt(n)), math.ceil(n / 16.0))))
+    reading takes max(4 sqrt(n), n/16), at most n and 1024: 128 at n = 1024,
+    1024 at n = 16384 and at n = 65536 (the fit's cost grows like
+    n N_r^2 + N_r^3 while the PCG products fall slowly with N_r)."""
+    return int(min(n, 1024, max(math.ceil(4.0 * math.sqrt(n)), math.ceil(n / 16.0))))
 
 
 # Configurations of the workloads (sizes and field parameters).

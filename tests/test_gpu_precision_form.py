@@ -1,7 +1,7 @@
 """The precision form at its full size: n = 65536 uniform locations, d = 64,
 lambda = 1e-4, 8 transmitters, matrix-free split-bf16 operator with the
 float64-accurate residual every 20 products, N_r from the default schedule
-(2048), tolerance 1e-6 on the true residual; compared with a float64 GPU run
+(1024), tolerance 1e-6 on the true residual; compared with a float64 GPU run
 of the same instance (materialised float64 operator, float64 PCG), and the
 same generator at n = 8192 against the float64 oracle.
 
@@ -65,7 +65,7 @@ def test_precision_form_n8192_against_oracle(L):
 
 
 def test_precision_form_full_size_against_float64_gpu(L):
-    """n = 65536, d = 64: the mixed form (tcgen05 operator, N_r = 2048) against
+    """n = 65536, d = 64: the mixed form (tcgen05 operator, N_r = 1024) against
     a float64 GPU run of the same instance (float64 operator and PCG, CCCP with
     N_r = 512 for time): both meet the true tolerance by the float64 operator;
     alpha error of the mixed run relative to the float64 run and the map
@@ -82,7 +82,7 @@ def test_precision_form_full_size_against_float64_gpu(L):
     # mixed form
     op = L.laker_build_kernel(ctx, _dev(inst.Q), inst.scale, inst.lam, L.BF16X3)
     n_r = synth.default_num_directions(n)
-    assert n_r == 2048
+    assert n_r == 1024
     P = L.laker_fit_preconditioner(ctx, op, _dev(synth.directions(n, n_r, 3003)))
     am, im = L.laker_pcg_solve(ctx, op, P, y, c["tol"], max_iter=40000, refine_every=20)
     w = torch.empty_like(am)
