@@ -188,7 +188,9 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
                                            ctx->stream));
         }
     }
-    if (mode == 2) {
+    if (mode == 2 && d <= 64) {
+        if ((st = resid_build_df(ctx, op)) != LAKER_OK) return st;
+    } else if (mode == 2) {
         const int nb128 = (int)((n + 127) / 128);
         const int nt = 2 * nb128;   // 64-blocks, padded so that every packed tile is written
         const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
@@ -204,7 +206,7 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
             k_build_sym<0><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64, nullptr,
                                                                      nullptr, op->ldk, nt);
     }
-    LK_LAUNCHED(ctx);
+    if (!(mode == 2 && d <= 64)) LK_LAUNCHED(ctx);
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->lambda,
                                                                  op->diagA);
     LK_LAUNCHED(ctx);

@@ -184,6 +184,73 @@ __global__ void k_df_sym_finish(RSched sch, int64_t n, double lambda, const doub
     w[i] = fma(lambda, x[i], lk::df_to(s));
 }
 
+// Packed pair (hi, lo) of the upper-triangular tiles in double-float on the
+// float32 pipes (GB300's float64 rate is ~1/64 of float32): each thread takes
+// one column j of a tile (its embedding row, pre-scaled by sqrt(scale), in
+// registers) and half of the rows i (from shared memory); the logit is a
+// compensated dot product (Dot3, error ~2^-70 of the sum of |terms|) and the
+// exponential Tang's double-float exp (~1e-14 relative), so hi + lo is G_ij
+// to ~2^-46.  Stores are coalesced along j.  Entries with i or j >= n are 0.
+template <int DM>
+__global__ void __launch_bounds__(256)
+k_build_packed_df(const float2* __restrict__ Qs, int64_t n, int d, int nb, float* __restrict__ Kp) {
+    extern __shared__ float2 qi_s[];             // 128 rows x DM df values of block I
+    __shared__ float e2tab[128];
+    lk::df_exp_table_init(e2tab);
+    const int64_t t = blockIdx.x;
+    int I = 0;
+    while (I + 1 < nb && r_row_start(I + 1, nb) <= t) ++I;
+    const int J = I + (int)(t - r_row_start(I, nb));
+    for (int idx = threadIdx.x; idx < RT * DM; idx += blockDim.x) {
+        const int r = idx / DM, k = idx % DM;
+        const int64_t i = (int64_t)I * RT + r;
+        qi_s[idx] = (i < n && k < d) ? Qs[i * d + k] : make_float2(0.f, 0.f);
+    }
+    const int c = threadIdx.x & (RT - 1), half = threadIdx.x >> 7;
+    const int64_t j = (int64_t)J * RT + c;
+    lk::df2 qj[DM];
+#pragma unroll
+    for (int k = 0; k < DM; ++k) {
+        const float2 v = (j < n && k < d) ? Qs[j * d + k] : make_float2(0.f, 0.f);
+        qj[k] = {v.x, v.y};
+    }
+    __syncthreads();
+    float* hi = Kp + t * (2 * RT * RT);
+    float* lo = hi + RT * RT;
+    // four rows at a time: four independent compensated dot products in flight
+    for (int r0 = half * (RT / 2); r0 < (half + 1) * (RT / 2); r0 += 4) {
+        lk::Dot3 dot[4];
+#pragma unroll
+        for (int k = 0; k < DM; ++k) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 q = qi_s[(r0 + u) * DM + k];
+                dot[u].add(lk::df2{q.x, q.y}, qj[k]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u;
+            const int64_t i = (int64_t)I * RT + r;
+            float h = 0.f, l = 0.f;
+            if (i < n && j < n) {
+                const lk::df2 e = lk::df_exp(dot[u].value(), e2tab);
+                h = e.hi;
+                l = e.lo;
+            }
+            hi[r * RT + c] = h;
+            lo[r * RT + c] = l;
+        }
+    }
+}
+
+__global__ void k_q_df(int64_t count, const double* __restrict__ x, double scale, float2* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const lk::df2 v = lk::df_from(x[i] * scale);
+    y[i] = make_float2(v.hi, v.lo);
+}
+
 }  // namespace
 
 struct ResidWork {
@@ -244,5 +311,32 @@ laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, d
     k_df_sym_finish<<<(unsigned)rw->sch.nb, RT, 0, ctx->stream>>>(rw->sch, op->n, op->lambda, x, rw->rowpart,
                                                                     rw->colpart, rw->nslots, w, sc, gate);
     LK_LAUNCHED(ctx);
+    return LAKER_OK;
+}
+
+// Fill the packed pair of a split-bf16 operator (d <= 64) in double-float.
+laker_status resid_build_df(laker_ctx* ctx, const laker_op* op) {
+    const ResidWork* rw = static_cast<const ResidWork*>(op->rw);
+    if (!rw) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "packed pair not allocated");
+    const int64_t n = op->n;
+    const int d = op->d;
+    float2* Qs = nullptr;
+    laker_status st = lk_malloc(ctx, (void**)&Qs, (size_t)n * d * sizeof(float2));
+    if (st != LAKER_OK) return st;
+    k_q_df<<<(unsigned)((n * d + 255) / 256), 256, 0, ctx->stream>>>(n * d, op->Q64, std::sqrt(op->scale), Qs);
+    LK_LAUNCHED(ctx);
+    const int dm = d <= 16 ? 16 : d <= 32 ? 32 : 64;
+    const size_t smem = (size_t)RT * dm * sizeof(float2);
+    cudaError_t e = cudaSuccess;
+#define LK_PB(D)                                                                                                  \
+    e = cudaFuncSetAttribute(k_build_packed_df<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    if (e == cudaSuccess)                                                                                         \
+        k_build_packed_df<D><<<(unsigned)rw->sch.T, 256, smem, ctx->stream>>>(Qs, n, d, rw->sch.nb, rw->Kp)
+    if (dm == 16) { LK_PB(16); } else if (dm == 32) { LK_PB(32); } else { LK_PB(64); }
+#undef LK_PB
+    if (e != cudaSuccess) { cudaFree(Qs); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    LK_LAUNCHED(ctx);
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(Qs);
     return LAKER_OK;
 }
