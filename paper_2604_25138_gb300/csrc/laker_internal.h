@@ -149,6 +149,7 @@ laker_status dirs_tc(laker_ctx* ctx, const laker_op* op, const double* Z, int nr
 laker_status resid_prepare(laker_ctx* ctx, laker_op* op, float** Kp);
 void resid_release(laker_op* op);
 laker_status resid_build_df(laker_ctx* ctx, const laker_op* op);
+laker_status resid_status(laker_ctx* ctx, const laker_op* op);
 laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w, const PcgScalars* sc,
                           int gate);
 // laker_rng.cu (Philox4x32-10 Gaussian directions, n_r-major rows)

@@ -796,7 +796,10 @@ laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x
 }
 
 laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w) {
-    if (op->rw) return resid_matvec(ctx, op, x, w, nullptr, 0);
+    if (op->rw) {
+        const laker_status st = resid_matvec(ctx, op, x, w, nullptr, 0);
+        return st != LAKER_OK ? st : resid_status(ctx, op);
+    }
     if (op->precision != LAKER_FP64) return launch_mv_df(ctx, op, x, w, nullptr, GATE_NONE, mv_blocks_for(ctx, op->n));
     return launch_mv<double>(ctx, op, op->K64, x, nullptr, nullptr, 0, w, nullptr, nullptr, GATE_NONE, 0,
                              mv_blocks_for(ctx, op->n));
@@ -988,6 +991,7 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     cudaGraphDestroy(graph);
     cudaFreeHost(flag_host);
     if (op->variant == LAKER_MATRIX_FREE && (st = mf_status(ctx, op)) != LAKER_OK) { ws_free(ws); return st; }
+    if ((st = resid_status(ctx, op)) != LAKER_OK) { ws_free(ws); return st; }
 
     // final report: float64-accurate residual of the returned alpha
     if ((st = op_matvec_fp64(ctx, op, alpha, ws.w2)) != LAKER_OK) { ws_free(ws); return st; }

@@ -26,6 +26,7 @@
 
 #include "laker_device.cuh"
 #include "laker_df.cuh"
+#include "laker_tc.cuh"
 
 namespace {
 
@@ -69,19 +70,79 @@ __device__ __forceinline__ lk::df2 shfl_df(lk::df2 v, int o) {
     return u;
 }
 
-__global__ void __launch_bounds__(RW * 32, 1)
+constexpr int RQ = 32;                       // rows of a quarter tile (one pipeline stage)
+constexpr int RSTAGES = 5;
+constexpr uint32_t RQ_BYTES = RQ * RT * 4;   // one quarter of hi (or lo): 16 KB
+constexpr int R_THREADS = (RW + 1) * 32;     // 16 compute warps + one copy warp
+
+struct RSmem {
+    uint64_t full[RSTAGES];
+    uint64_t empty[RSTAGES];
+};
+
+size_t r_smem_bytes() { return 128 + (size_t)RSTAGES * 2 * RQ_BYTES + sizeof(RSmem); }
+
+// One CTA per SM over a contiguous range of the tiles.  A copy warp streams
+// each tile as four quarters (32 rows of hi, then of lo: 2 x 16 KB contiguous
+// bulk copies) through a 5-stage shared-memory ring; 16 compute warps take 2
+// rows of each quarter (warp w: rows 2w, 2w + 1 of the quarter, i.e. rows
+// 32 q + 2w + {0, 1} of the tile) and lane l the columns 4l .. 4l + 3.
+__global__ void __launch_bounds__(R_THREADS, 1)
 k_df_sym(const float* __restrict__ Kp, RSched sch, int64_t n, const double* __restrict__ x,
-         float2* __restrict__ rowpart, float2* __restrict__ colpart, const PcgScalars* sc, int gate) {
+         float2* __restrict__ rowpart, float2* __restrict__ colpart, const PcgScalars* sc, int gate,
+         int* __restrict__ err) {
     if (r_gated(sc, gate)) return;
     __shared__ float2 xI[RT], xJ[RT];
     __shared__ float2 cred[RW][RT];
+    extern __shared__ __align__(128) unsigned char r_smem_raw[];
+    unsigned char* base = r_smem_raw;
+    {
+        const uint32_t a = smem_u32(base);
+        base += (128 - (a & 127)) & 127;
+    }
+    float* ring = reinterpret_cast<float*>(base);                          // [stage][hi 32 x 128][lo 32 x 128]
+    RSmem* S = reinterpret_cast<RSmem*>(base + (size_t)RSTAGES * 2 * RQ_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x;
     const int64_t t0 = r_begin(g, sch), t1 = r_begin(g + 1, sch);
     if (t0 >= t1) return;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < RSTAGES; ++st) { mbar_init(&S->full[st], 1); mbar_init(&S->empty[st], RW); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int64_t nq = (t1 - t0) * 4;    // quarters this CTA streams
+    if (warp == RW) {
+        // ---------------- copy warp ----------------
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t q = 0; q < nq; ++q) {
+                const int st = (int)(q % RSTAGES);
+                if (!mbar_wait(&S->empty[st], (uint32_t)((q / RSTAGES) & 1) ^ 1, err)) break;
+                const int64_t t = t0 + q / 4;
+                const int part = (int)(q % 4);
+                const float* hi = Kp + t * (2 * RT * RT) + part * RQ * RT;
+                float* dst = ring + (size_t)st * 2 * RQ * RT;
+                mbar_expect_tx(&S->full[st], 2 * RQ_BYTES);
+                bulk_load(dst, hi, RQ_BYTES, &S->full[st]);
+                bulk_load(dst + RQ * RT, hi + RT * RT, RQ_BYTES, &S->full[st]);
+                issued = q + 1;
+            }
+            for (int64_t q = (issued > RSTAGES ? issued - RSTAGES : 0); q < issued; ++q) {
+                const long long c0 = clock64();
+                while (!mbar_try_wait(&S->full[q % RSTAGES], (uint32_t)((q / RSTAGES) & 1)) &&
+                       clock64() - c0 < TC_SPIN_CYCLES) {
+                }
+            }
+        }
+        // the copy warp joins no further barrier: compute warps sync with named barrier 1
+        return;
+    }
+    // ---------------- compute warps ----------------
+    auto csync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(RW * 32) : "memory"); };
     int I = r_row_of(t0, sch.nb);
     int J = I + (int)(t0 - r_row_start(I, sch.nb));
-    lk::Dot3 row[RR];
+    lk::Dot3 row[8];   // rows 32 qq + 2 warp + e of block I, qq = 0..3, e = 0..1
     auto load_x = [&](float2* dst, int blk) {
         if (threadIdx.x < RT) {
             const int64_t i = (int64_t)blk * RT + threadIdx.x;
@@ -92,46 +153,60 @@ k_df_sym(const float* __restrict__ Kp, RSched sch, int64_t n, const double* __re
     auto flush = [&](int blk) {
         const int slot = g - r_owner(r_row_start(blk, sch.nb), sch);
 #pragma unroll
-        for (int k = 0; k < RR; ++k) {
+        for (int k = 0; k < 8; ++k) {
             lk::df2 v = row[k].value();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = lk::df_add(v, shfl_df(v, o));
-            if (lane == 0)
-                rowpart[((int64_t)blk * sch.slots + slot) * RT + warp * RR + k] = make_float2(v.hi, v.lo);
+            if (lane == 0) {
+                const int r = (k >> 1) * RQ + 2 * warp + (k & 1);
+                rowpart[((int64_t)blk * sch.slots + slot) * RT + r] = make_float2(v.hi, v.lo);
+            }
             row[k] = lk::Dot3();
         }
     };
     load_x(xI, I);
-    bool dirty = false;   // row sums of block I accumulated since the last flush
+    bool dirty = false;
+    // once a bounded wait has expired (the error word is set) a warp skips its
+    // waits and arithmetic but keeps reaching every named barrier, so that all
+    // compute warps leave the loop together
+    bool ok = true;
+    int64_t q = 0;
     for (int64_t t = t0; t < t1; ++t) {
         load_x(xJ, J);
-        __syncthreads();
-        const float* hi = Kp + t * (2 * RT * RT);
-        const float* lo = hi + RT * RT;
-        float4 h[RR], l[RR];
-#pragma unroll
-        for (int k = 0; k < RR; ++k) {
-            const int r = warp * RR + k;
-            h[k] = __ldcs(reinterpret_cast<const float4*>(hi + r * RT) + lane);
-            l[k] = __ldcs(reinterpret_cast<const float4*>(lo + r * RT) + lane);
-        }
+        csync();
         lk::df2 xj[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) { const float2 v = xJ[4 * lane + c]; xj[c] = {v.x, v.y}; }
         const bool diag = (I == J);
         lk::Dot3 col[4];
 #pragma unroll
-        for (int k = 0; k < RR; ++k) {
-            const float gh[4] = {h[k].x, h[k].y, h[k].z, h[k].w};
-            const float gl[4] = {l[k].x, l[k].y, l[k].z, l[k].w};
-            const float2 xv = xI[warp * RR + k];
-            const lk::df2 xi = {xv.x, xv.y};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const lk::df2 gv = {gh[c], gl[c]};
-                row[k].add(gv, xj[c]);
-                if (!diag) col[c].add(gv, xi);
+        for (int part = 0; part < 4; ++part, ++q) {
+            const int st = (int)(q % RSTAGES);
+            if (ok) {
+                int w = (lane == 0) ? (int)mbar_wait(&S->full[st], (uint32_t)((q / RSTAGES) & 1), err) : 0;
+                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
             }
+            if (!ok) continue;
+            const float* hq = ring + (size_t)st * 2 * RQ * RT;
+            const float* lq = hq + RQ * RT;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rr = 2 * warp + e;                       // row within the quarter
+                const float4 h = reinterpret_cast<const float4*>(hq + rr * RT)[lane];
+                const float4 l = reinterpret_cast<const float4*>(lq + rr * RT)[lane];
+                const float gh[4] = {h.x, h.y, h.z, h.w};
+                const float gl[4] = {l.x, l.y, l.z, l.w};
+                const float2 xv = xI[part * RQ + rr];
+                const lk::df2 xi = {xv.x, xv.y};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const lk::df2 gv = {gh[c], gl[c]};
+                    row[2 * part + e].add(gv, xj[c]);
+                    if (!diag) col[c].add(gv, xi);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S->empty[st]);
         }
         dirty = true;
         if (!diag) {
@@ -141,23 +216,22 @@ k_df_sym(const float* __restrict__ Kp, RSched sch, int64_t n, const double* __re
                 cred[warp][4 * lane + c] = make_float2(v.hi, v.lo);
             }
         }
-        __syncthreads();
+        csync();
         if (!diag && threadIdx.x < RT) {
             lk::df2 s = {cred[0][threadIdx.x].x, cred[0][threadIdx.x].y};
 #pragma unroll
             for (int w = 1; w < RW; ++w) s = lk::df_add(s, lk::df2{cred[w][threadIdx.x].x, cred[w][threadIdx.x].y});
             colpart[t * RT + threadIdx.x] = make_float2(s.hi, s.lo);
         }
-        // the last tile of block row I: flush this CTA's segment of it
         if (++J == sch.nb) {
             flush(I);
             dirty = false;
             ++I;
             J = I;
-            if (t + 1 < t1) load_x(xI, I);   // xI is not read again before the next barrier
+            if (t + 1 < t1) load_x(xI, I);
         }
     }
-    if (dirty) flush(I);
+    if (ok && dirty) flush(I);
 }
 
 // w_i = lambda x_i + (row partials of block I's segments) + (column partials of
@@ -259,6 +333,7 @@ struct ResidWork {
     float2* rowpart = nullptr;
     float2* colpart = nullptr;
     int* nslots = nullptr;
+    int* err = nullptr;           // status word of the bounded waits
 };
 
 void resid_release(laker_op* op) {
@@ -268,6 +343,7 @@ void resid_release(laker_op* op) {
     cudaFree(rw->rowpart);
     cudaFree(rw->colpart);
     cudaFree(rw->nslots);
+    cudaFree(rw->err);
     delete rw;
     op->rw = nullptr;
 }
@@ -293,6 +369,9 @@ laker_status resid_prepare(laker_ctx* ctx, laker_op* op, float** Kp) {
         return st;
     if ((st = lk_malloc(ctx, (void**)&rw->colpart, (size_t)s.T * RT * sizeof(float2))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&rw->nslots, (size_t)s.nb * sizeof(int))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&rw->err, sizeof(int))) != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMemsetAsync(rw->err, 0, sizeof(int), ctx->stream));
+    LK_CUDA(ctx, cudaFuncSetAttribute(k_df_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem_bytes()));
     LK_CUDA(ctx, cudaMemcpyAsync(rw->nslots, ns.data(), sizeof(int) * s.nb, cudaMemcpyHostToDevice, ctx->stream));
     LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     *Kp = rw->Kp;
@@ -305,8 +384,8 @@ laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, d
                           int gate) {
     const ResidWork* rw = static_cast<const ResidWork*>(op->rw);
     if (!rw) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "packed float64-accurate operator not built");
-    k_df_sym<<<(unsigned)rw->sch.G, RW * 32, 0, ctx->stream>>>(rw->Kp, rw->sch, op->n, x, rw->rowpart, rw->colpart,
-                                                                  sc, gate);
+    k_df_sym<<<(unsigned)rw->sch.G, R_THREADS, r_smem_bytes(), ctx->stream>>>(rw->Kp, rw->sch, op->n, x, rw->rowpart,
+                                                                              rw->colpart, sc, gate, rw->err);
     LK_LAUNCHED(ctx);
     k_df_sym_finish<<<(unsigned)rw->sch.nb, RT, 0, ctx->stream>>>(rw->sch, op->n, op->lambda, x, rw->rowpart,
                                                                     rw->colpart, rw->nslots, w, sc, gate);
@@ -339,4 +418,17 @@ laker_status resid_build_df(laker_ctx* ctx, const laker_op* op) {
     LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(Qs);
     return LAKER_OK;
+}
+
+// Status of the bounded waits of the float64-accurate product (synchronises
+// the stream); LAKER_ERR_TIMEOUT if one expired, and the word is cleared.
+laker_status resid_status(laker_ctx* ctx, const laker_op* op) {
+    const ResidWork* rw = static_cast<const ResidWork*>(op->rw);
+    if (!rw) return LAKER_OK;
+    int h = 0;
+    LK_CUDA(ctx, cudaMemcpyAsync(&h, rw->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!h) return LAKER_OK;
+    LK_CUDA(ctx, cudaMemsetAsync(rw->err, 0, sizeof(int), ctx->stream));
+    return set_error(ctx, (laker_status)h, "float64-accurate product: bounded wait expired");
 }

@@ -64,6 +64,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Contiguous bulk copy of `bytes` (multiple of 16, both addresses 16-byte
+// aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // tcgen05 shared-memory matrix descriptor, K-major operand with a swizzle of
 // `swz_bytes` (32/64/128) per row: SBO = 8 rows, LBO unused for swizzled
 // K-major layouts, fixed version bits 46..48 = 0b001.
