@@ -4,13 +4,15 @@ profiling one kernel at a time with Nsight Compute.
     python -m paper_2604_25138_gb300.profile_cases operator --n 16384 --precision bf16x3 --reps 5
     python -m paper_2604_25138_gb300.profile_cases fit --n 16384
     python -m paper_2604_25138_gb300.profile_cases solve --n 16384
+    python -m paper_2604_25138_gb300.profile_cases residual --n 16384 --d 64 --reps 3
 
 `operator` builds the operator of the benchmark instance (clustered layout,
 d = 32, lambda = 1e-4) and applies it `reps` times; `fit` builds it and fits
 the CCCP preconditioner only (printing how many kernels ran before the fit, for
 a launch window over the fit); `solve` also fits the CCCP
 preconditioner (N_r from the default schedule) and runs the mixed PCG solve;
-`map` evaluates the radio map on a grid of m points.  All inputs are the seeded
+`map` evaluates the radio map on a grid of m points; `residual` applies the
+float64-accurate product (the true residual of mixed solves) `reps` times.  All inputs are the seeded
 synthetic ones of `synth.py`; nothing here is timed for reporting.
 """
 import argparse
@@ -26,7 +28,7 @@ PRECISIONS = {"fp64": L.FP64, "fp32": L.FP32, "bf16x3": L.BF16X3}
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["operator", "fit", "solve", "map"])
+    ap.add_argument("case", choices=["operator", "fit", "solve", "map", "residual"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--d", type=int, default=32)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16x3")
@@ -39,13 +41,13 @@ def main(argv=None):
     dev = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     ctx = L.Context(0)
     op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, PRECISIONS[a.precision])
-    if a.case == "operator":
+    if a.case in ("operator", "residual"):
         x = dev(synth.random_vector(a.n, a.seed))
         w = torch.empty_like(x)
         for _ in range(a.reps):
-            L.laker_op_matvec(ctx, op, x, w)
+            L.laker_op_matvec(ctx, op, x, w, fp64=(a.case == "residual"))
         torch.cuda.synchronize()
-        print(f"operator n={a.n} d={a.d} {a.precision}: {a.reps} products, |w| = {float(w.norm()):.6e}")
+        print(f"{a.case} n={a.n} d={a.d} {a.precision}: {a.reps} products, |w| = {float(w.norm()):.6e}")
         return
     Z = dev(synth.directions(a.n, synth.default_num_directions(a.n), a.seed))
     torch.cuda.synchronize()
