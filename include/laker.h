@@ -108,9 +108,14 @@ laker_status laker_set_wait_budget(laker_ctx* ctx, int64_t cycles);
  *   scale   1.0 reproduces the paper's exp(<e_i,e_j>); 1/sqrt(d) gives the
  *           scaled dot-product form.
  *   lambda  ridge parameter, must be > 0.
- *   precision / variant  see the enums.  FP32 and BF16X3 operators keep G as a
- *           float32 pair (hi, lo) with hi + lo equal to G to ~2^-48: hi is the
- *           float32 operator, hi + lo gives float64-accurate true residuals.
+ *   precision / variant  see the enums.  FP32 operators keep G as a float32
+ *           pair (hi, lo), n x n each, with hi + lo equal to G to ~2^-48: hi
+ *           is the float32 operator, hi + lo gives float64-accurate true
+ *           residuals.  BF16X3 operators are matrix-free for their products
+ *           and keep the pair only for the upper triangle (128 x 128 tiles,
+ *           n^2/2 x 8 bytes, built in double-float) for the float64-accurate
+ *           product.  FP32 and BF16X3 operators with d <= 64 also keep the
+ *           split-bf16 embedding for the tensor-core kernels.
  * Errors: LAKER_ERR_ARG for n < 1, d < 1 or d > 256, lambda <= 0;
  *         LAKER_ERR_OOM if G does not fit.
  */
@@ -158,13 +163,17 @@ laker_status laker_op_time_product(laker_ctx* ctx, const laker_op* op, const dou
  *           (1e-3 when n_r >= n).
  *   eps     safeguard of F_gamma (> 0).
  * Precision: float64 throughout for FP64 operators.  For FP32 and BF16X3
- * operators the products G z_k use the materialised float32 G through cuBLAS
- * (bf16x9 float32 emulation on the tensor cores; a cuBLAS handle is created
- * on the context's first fit and released by laker_destroy), and P is kept in
- * the orthonormal form c^-1/2 I + U~ diag(phi) U~^T over the eigen-directions
+ * operators (d <= 64) the directions are z~_k = bf16(z_k) (round to nearest
+ * even; still standard-normal to 2^-9) and u_k = (lambda I + G) z~_k comes
+ * from a tensor-core kernel that recomputes each 128 x 128 tile of G from
+ * the embedding and multiplies it, as bf16 hi + lo, into all directions at
+ * once (~1e-5 relative; G is never formed); for d > 64 from the float32 G.
+ * P is kept in the orthonormal form c^-1/2 I + U~ diag(phi) U~^T over the
+ * eigen-directions
  * of D^1/2 M D^1/2 with eigenvalue > 1e-3 c (float32 U~).
  * Errors: LAKER_ERR_ARG for n_r < 1 or n_r > 2048; LAKER_ERR_NOT_SPD if a
- * factorisation fails; LAKER_ERR_CUDA if cuBLAS fails.
+ * factorisation fails; LAKER_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core directions kernel expired.
  */
 laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const double* Z,
                                       int n_r, double gamma, double rho, double eps,
