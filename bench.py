@@ -637,6 +637,40 @@ def run_sweep(args):
     print(json.dumps(line))
 
 
+def run_variants(args):
+    """The per-n choice of the float32-class operator: for n from 512 to
+    32768 (d = 32, the c2 field and layout), an FP32 operator built with
+    LAKER_AUTO times one product of the materialised variant (stream of the
+    float32 G) and of the matrix-free one (split-bf16 tcgen05 kernel) and keeps
+    the faster; the line reports both times, the choice, and the algorithmic
+    HBM rate of the materialised product."""
+    import torch
+
+    from paper_2604_25138_gb300 import build
+    from paper_2604_25138_gb300 import laker as L
+
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = L.Context(0)
+    dev_t = torch.device("cuda", 0)
+    rows = []
+    for n in args.variant_sizes:
+        inst = synth.make_instance(n, 32, 1e-4, n_tx=8, seed=2000 + n, layout="clustered", grid=2)
+        Q = torch.as_tensor(np.ascontiguousarray(inst.Q), dtype=torch.float64, device=dev_t)
+        op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32, L.AUTO)
+        dsc = L.laker_op_describe(op)
+        x = torch.ones(n, dtype=torch.float64, device=dev_t)
+        t_kept = L.laker_op_time_product(ctx, op, x, reps=20)
+        ldk = (n + 3) // 4 * 4
+        rows.append({"n": n, "t_materialised_ms": dsc["t_materialised_ms"], "t_matrix_free_ms": dsc["t_matrix_free_ms"],
+                     "chosen": "matrix-free" if dsc["variant"] == L.MATRIX_FREE else "materialised",
+                     "t_chosen_ms_20reps": t_kept,
+                     "materialised_gbs": (n * ldk * 4 + 3 * n * 8) / (dsc["t_materialised_ms"] * 1e-3) / 1e9})
+        op.close()
+    print(json.dumps({"metric": "float32-class operator: variant chosen per n (AUTO)", "rows": rows,
+                      "peak_hbm_gbs": peaks()[0]}))
+
+
 # ---------------------------------------------------------------------------
 # The FP64 oracle on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
@@ -730,7 +764,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[50, 200, 500, 1000, 2000, 4000, 8000])
     ap.add_argument("--gd-steps", type=int, default=2000)
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "batched", "learned", "sweep"],
+    ap.add_argument("--variant-sizes", type=int, nargs="+", default=[512, 1024, 2048, 4096, 8192, 16384, 32768])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "batched", "learned", "sweep", "variants"],
                     help="c3: the precision-form instance n=65536, d=64 (the headline line); c2: the n=16384 "
                          "instance; batched: 256 instances; learned: the set-network preconditioner")
     ap.add_argument("--learned-train", type=int, default=256)
@@ -746,6 +781,8 @@ def main():
         run_learned(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "variants":
+        run_variants(args)
     else:
         run_ours(args)
 

@@ -50,7 +50,12 @@ typedef enum {
                             cores, float32 exp2 and sums; matrix-free */
 } laker_precision;
 
-/* How the operator v -> (lambda I + G) v is evaluated. */
+/* How the operator v -> (lambda I + G) v is evaluated.  FP64 operators are
+ * materialised; BF16X3 operators are matrix-free; FP32 operators with
+ * d <= 64 have both variants (the matrix-free one recomputes G with the
+ * split-bf16 tensor-core kernel, ~1e-6 relative), and LAKER_AUTO times one
+ * product of each after the build and keeps the faster for this n (the
+ * choice and both times are reported by laker_op_describe). */
 typedef enum {
     LAKER_AUTO = 0,
     LAKER_MATERIALISED = 1,   /* G stored in HBM, streamed each product */
@@ -117,12 +122,21 @@ laker_status laker_set_wait_budget(laker_ctx* ctx, int64_t cycles);
  *           product.  FP32 and BF16X3 operators with d <= 64 also keep the
  *           split-bf16 embedding for the tensor-core kernels.
  * Errors: LAKER_ERR_ARG for n < 1, d < 1 or d > 256, lambda <= 0;
- *         LAKER_ERR_OOM if G does not fit.
+ *         LAKER_ERR_UNSUPPORTED for a matrix-free FP64 operator, or a
+ *         matrix-free FP32 / BF16X3 one with d > 64; LAKER_ERR_OOM if G does
+ *         not fit.
  */
 laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int d,
                                 double scale, double lambda, int precision, int variant,
                                 laker_op** op);
 laker_status laker_op_destroy(laker_op* op);
+/* The operator's precision and the variant its products use; for an FP32
+ * operator built with LAKER_AUTO also the measured time of one product of
+ * each variant (ms; 0 when not measured).  Any output pointer may be NULL.
+ * Errors: LAKER_ERR_ARG for a NULL operator. */
+laker_status laker_op_describe(const laker_op* op, int* precision, int* variant, double* t_materialised_ms,
+                               double* t_matrix_free_ms);
+
 
 /* w = (lambda I + G) x with the operator's inner precision (device n-vectors). */
 laker_status laker_op_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w);

@@ -154,11 +154,18 @@ laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int 
     if (!std::isfinite(scale)) return set_error(ctx, LAKER_ERR_ARG, "scale not finite");
     if (precision < LAKER_FP64 || precision > LAKER_BF16X3) return set_error(ctx, LAKER_ERR_ARG, "bad precision");
     if (variant < LAKER_AUTO || variant > LAKER_MATRIX_FREE) return set_error(ctx, LAKER_ERR_ARG, "bad variant");
+    // split-bf16 operators are matrix-free; float64 operators are materialised;
+    // float32 operators (d <= 64, scale > 0) have both variants, and AUTO
+    // times one product of each after the build and keeps the faster
+    const bool fp32_mf_ok = precision == LAKER_FP32 && d <= 64 && scale > 0.0;
+    const bool autotune = variant == LAKER_AUTO && fp32_mf_ok;
     if (variant == LAKER_AUTO)
         variant = (precision == LAKER_BF16X3) ? LAKER_MATRIX_FREE : LAKER_MATERIALISED;
     if (precision == LAKER_BF16X3) variant = LAKER_MATRIX_FREE;
-    if (precision != LAKER_BF16X3 && variant == LAKER_MATRIX_FREE)
-        return set_error(ctx, LAKER_ERR_UNSUPPORTED, "the matrix-free operator uses split-bf16 logits (BF16X3)");
+    if (precision == LAKER_FP64 && variant == LAKER_MATRIX_FREE)
+        return set_error(ctx, LAKER_ERR_UNSUPPORTED, "float64 operators are materialised only");
+    if (precision == LAKER_FP32 && variant == LAKER_MATRIX_FREE && !fp32_mf_ok)
+        return set_error(ctx, LAKER_ERR_UNSUPPORTED, "the matrix-free float32 operator needs d <= 64 and scale > 0");
     if ((st = scan_finite(ctx, Q, n * d)) != LAKER_OK) return st;
     laker_op* op = new (std::nothrow) laker_op();
     if (!op) return LAKER_ERR_OOM;
@@ -173,9 +180,43 @@ laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int 
     cudaError_t e = cudaMemcpyAsync(op->Q64, Q, (size_t)n * d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) { free_op(op); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
     if ((st = build_operator(ctx, op)) != LAKER_OK) { free_op(op); return st; }
+    if (precision == LAKER_FP32 && (variant == LAKER_MATRIX_FREE || autotune)) {
+        if ((st = mf_prepare(ctx, op)) != LAKER_OK) { free_op(op); return st; }
+    }
+    if (autotune) {
+        // one product of each variant on y = 1 (after a warm-up each), CUDA events
+        double* x = nullptr;
+        if ((st = lk_malloc(ctx, (void**)&x, (size_t)n * sizeof(double))) != LAKER_OK) { free_op(op); return st; }
+        std::vector<double> ones((size_t)n, 1.0);
+        e = cudaMemcpyAsync(x, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        double tm = 0.0, tf = 0.0;
+        if (e == cudaSuccess) {
+            op->variant = LAKER_MATERIALISED;
+            st = op_time_product(ctx, op, x, 3, &tm);
+            op->variant = LAKER_MATRIX_FREE;
+            if (st == LAKER_OK) st = op_time_product(ctx, op, x, 3, &tf);
+        }
+        cudaFree(x);
+        if (e != cudaSuccess) { free_op(op); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+        if (st != LAKER_OK) { free_op(op); return st; }
+        op->t_mat_ms = tm;
+        op->t_mf_ms = tf;
+        op->variant = (tf < tm) ? LAKER_MATRIX_FREE : LAKER_MATERIALISED;
+    }
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) { free_op(op); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
     *out = op;
+    return LAKER_OK;
+}
+
+laker_status laker_op_describe(const laker_op* op, int* precision, int* variant, double* t_materialised_ms,
+                               double* t_matrix_free_ms) {
+    if (!op) return LAKER_ERR_ARG;
+    if (precision) *precision = op->precision;
+    if (variant) *variant = op->variant;
+    if (t_materialised_ms) *t_materialised_ms = op->t_mat_ms;
+    if (t_matrix_free_ms) *t_matrix_free_ms = op->t_mf_ms;
     return LAKER_OK;
 }
 

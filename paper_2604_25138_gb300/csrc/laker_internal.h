@@ -64,6 +64,8 @@ struct laker_op {
     double* diagA = nullptr;  // n, lambda + G_ii
     void* mf = nullptr;       // matrix-free operator workspace (tensor maps, buffers)
     void* rw = nullptr;       // packed float32 pair and schedule of the float64-accurate product (BF16X3)
+    double t_mat_ms = 0.0;    // product times measured by the AUTO variant choice (0 if not measured)
+    double t_mf_ms = 0.0;
 };
 
 // Largest number of random directions N_r (a preconditioner apply keeps the

@@ -68,6 +68,7 @@ def library() -> ctypes.CDLL:
         "laker_launch_count": (i64, [vp]),
         "laker_build_kernel": (i32, [vp, vp, i64, i32, f64, f64, i32, i32, pvp]),
         "laker_op_destroy": (i32, [vp]),
+        "laker_op_describe": (i32, [vp, pi32, pi32, ctypes.POINTER(f64), ctypes.POINTER(f64)]),
         "laker_pcg_solve_batched": (i32, [vp, i32, ctypes.POINTER(BatchItem), f64, i32, i32,
                                           ctypes.POINTER(SolveInfo), ctypes.POINTER(f64)]),
         "laker_setnet_create": (i32, [vp, i32, i32, i32, ctypes.c_uint64, pvp]),
@@ -228,6 +229,17 @@ def laker_build_kernel(ctx: Context, Q: torch.Tensor, scale: float, lam: float, 
         ctx.check(library().laker_build_kernel(ctx.handle, _ptr(Q, "Q"), n, d, scale, lam, precision, variant,
                                                ctypes.byref(h)))
     return Operator(ctx, h, n, d, precision, variant, Q)
+
+
+def laker_op_describe(op: Operator) -> dict:
+    """The operator's precision, the variant its products use and, for an
+    FP32 operator built with AUTO, the measured time of each variant (ms)."""
+    p, v = ctypes.c_int(), ctypes.c_int()
+    tm, tf = ctypes.c_double(), ctypes.c_double()
+    st = library().laker_op_describe(op.handle, ctypes.byref(p), ctypes.byref(v), ctypes.byref(tm), ctypes.byref(tf))
+    if st != OK:
+        raise LakerError(st, "laker_op_describe")
+    return {"precision": p.value, "variant": v.value, "t_materialised_ms": tm.value, "t_matrix_free_ms": tf.value}
 
 
 def laker_op_matvec(ctx: Context, op: Operator, x: torch.Tensor, w: torch.Tensor | None = None,

@@ -24,6 +24,7 @@ from . import laker as L
 from . import synth
 
 PRECISIONS = {"fp64": L.FP64, "fp32": L.FP32, "bf16x3": L.BF16X3}
+VARIANTS = {"auto": L.AUTO, "materialised": L.MATERIALISED, "matrix-free": L.MATRIX_FREE}
 
 
 def main(argv=None):
@@ -32,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--d", type=int, default=32)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16x3")
+    ap.add_argument("--variant", choices=sorted(VARIANTS), default="auto")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--seed", type=int, default=2000)
@@ -40,7 +42,7 @@ def main(argv=None):
     inst = synth.make_instance(a.n, a.d, 1e-4, n_tx=8, seed=a.seed, layout="clustered", grid=a.grid)
     dev = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     ctx = L.Context(0)
-    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, PRECISIONS[a.precision])
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, PRECISIONS[a.precision], VARIANTS[a.variant])
     if a.case in ("operator", "residual"):
         x = dev(synth.random_vector(a.n, a.seed))
         w = torch.empty_like(x)

@@ -387,3 +387,42 @@ def test_mixed_directions_match_oracle(L, ctx, prec, n, d, n_r):
     bound = 8 * 2.0 ** -18 * np.sqrt(n) * np.linalg.norm(Z, axis=0) / np.linalg.norm(A @ Z, axis=0)
     assert np.all(err <= bound + 1e-9), np.max(err / bound)
     assert np.median(err) < 2e-5, np.median(err)
+
+
+@pytest.mark.parametrize("n,d", [(700, 16), (4097, 32), (2048, 64)])
+def test_fp32_matrix_free_variant_matches_oracle(L, ctx, n, d):
+    """FP32 operators (d <= 64) also have the matrix-free variant: the
+    split-bf16 tensor-core product (~1e-6 relative) with the full float32
+    pair kept for the float64-accurate product; a mixed solve on it reaches
+    the true tolerance by the oracle's operator."""
+    from tests.gpu_util import dev, host, rel
+    inst = _inst(n, d, 1e-4, 500 + n, layout="clustered")
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP32, L.MATRIX_FREE)
+    assert L.laker_op_describe(op)["variant"] == L.MATRIX_FREE
+    x = synth.random_vector(n, n)
+    assert rel(host(L.laker_op_matvec(ctx, op, dev(x))), A @ x) < 1e-5
+    assert rel(host(L.laker_op_matvec(ctx, op, dev(x), fp64=True)), A @ x) < 1e-13
+    P = L.laker_fit_preconditioner(ctx, op, dev(synth.directions(n, synth.default_num_directions(n), n)))
+    alpha, info = L.laker_pcg_solve(ctx, op, P, dev(inst.y), 1e-6, max_iter=20000, refine_every=20)
+    assert O.relative_residual(A, host(alpha), inst.y) <= 1e-6 * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("n", [1024, 16384])
+def test_auto_variant_keeps_the_faster_product(L, ctx, n):
+    """LAKER_AUTO on an FP32 operator times one product of each variant after
+    the build and keeps the faster; the product of the kept variant is
+    correct."""
+    from tests.gpu_util import dev, host, rel
+    inst = _inst(n, 32, 1e-4, 600 + n)
+    op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP32, L.AUTO)
+    dsc = L.laker_op_describe(op)
+    assert dsc["t_materialised_ms"] > 0 and dsc["t_matrix_free_ms"] > 0
+    faster = L.MATRIX_FREE if dsc["t_matrix_free_ms"] < dsc["t_materialised_ms"] else L.MATERIALISED
+    assert dsc["variant"] == faster, dsc
+    print(f"n={n}: materialised {dsc['t_materialised_ms']:.3f} ms, matrix-free {dsc['t_matrix_free_ms']:.3f} ms")
+    x = synth.random_vector(n, 3)
+    rows = np.arange(0, n, max(1, n // 64))
+    Gx = O.kernel_matrix(inst.Q[rows], inst.scale, inst.Q) @ x + inst.lam * x[rows]
+    w = host(L.laker_op_matvec(ctx, op, dev(x)))[rows]
+    assert rel(w, Gx) < 1e-5
