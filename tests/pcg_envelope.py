@@ -75,3 +75,18 @@ def within_envelope(k, env):
     of a dozen rounding samples covers only part of the index's spread."""
     w = max(1, env[1] - env[0])
     return env[0] - w <= k <= env[1] + w
+
+
+def tol_envelope(A, y, P, tol, n_perm=6, p_rel=1e-9, n_pert=6, seed=0, max_iter=100000):
+    """(min, max) of the oracle's stopping index at a tolerance (the number
+    of products of O.pcg) over the plain run, n_perm permuted summation
+    orders of A p and n_pert runs with relative noise p_rel in every
+    preconditioner apply."""
+    rng = np.random.default_rng(seed)
+    ks = [O.pcg(A, y, P, tol, max_iter=max_iter).iterations]
+    for _ in range(n_perm):
+        ks.append(O.pcg(_PermutedA(A, rng.permutation(len(y))), y, P, tol, max_iter=max_iter).iterations)
+    if P is not None:
+        for _ in range(n_pert):
+            ks.append(O.pcg(A, y, _NoisyP(P, p_rel, rng), tol, max_iter=max_iter).iterations)
+    return min(ks), max(ks)

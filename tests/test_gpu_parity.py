@@ -11,6 +11,7 @@ import pytest
 
 from oracle import laker_oracle as O
 from paper_2604_25138_gb300 import synth
+from tests.pcg_envelope import tol_envelope, within_envelope
 
 pytestmark = pytest.mark.gpu
 
@@ -159,9 +160,11 @@ def test_c1_end_to_end_fp64(L, ctx):
     """Plain FP64 single instance (n=1024, d=16, lambda=1e-3, 3 Tx, N_r=128,
     PCG to 1e-8, 64x64 map).  kappa(A) ~ 1e6: the fit must match the dense
     oracle; the PCG arithmetic is checked on a fixed number of steps and alpha
-    at tol 1e-10; at tol 1e-8 the stopping iteration is chaotic under rounding
-    (equivalent float64 constructions of the same P stop anywhere in 322..360),
-    so that count is compared within 15 % and alpha against the exact solution."""
+    at tol 1e-10; at tol 1e-8 the stopping iteration is decided by rounding
+    (equivalent float64 constructions of the same P stop anywhere in
+    322..360), so that count is checked against the oracle's own envelope
+    (summation-order permutations and per-apply noise at the measured
+    difference of the GPU's apply) and alpha against the exact solution."""
     from tests.gpu_util import dev, host, rel
     cfg = synth.CONFIGS["c1"]
     inst = synth.make_instance(cfg["n"], cfg["d"], cfg["lam"], n_tx=cfg["n_tx"], seed=1001, grid=cfg["grid"])
@@ -183,10 +186,14 @@ def test_c1_end_to_end_fp64(L, ctx):
     # converged to 1e-10: alpha parity
     a_t, _ = L.laker_pcg_solve(ctx, op, P, dev(inst.y), 1e-10)
     assert rel(host(a_t), O.pcg(A, inst.y, ref.P, 1e-10).alpha) < 1e-9
-    # the configuration's tolerance
+    # the configuration's tolerance: the stopping index against the oracle's
+    # own rounding envelope (see test_c1_stopping_index_five_seeds)
     alpha, info = L.laker_pcg_solve(ctx, op, P, dev(inst.y), cfg["tol"])
     a = host(alpha)
-    assert abs(info["iterations"] - ref.pcg.iterations) <= 0.15 * ref.pcg.iterations
+    v = synth.random_vector(n, 2)
+    pv_err = rel(host(L.laker_precond_apply(ctx, P, dev(v))), ref.P @ v)
+    env = tol_envelope(A, inst.y, ref.P, cfg["tol"], p_rel=max(pv_err, 1e-15))
+    assert within_envelope(info["iterations"], env), (info["iterations"], env)
     assert O.relative_residual(A, a, inst.y) <= 1e-8 * 1.01
     a_star = O.solve_direct(A, inst.y)
     assert rel(a, a_star) < 1e-8
@@ -426,3 +433,34 @@ def test_auto_variant_keeps_the_faster_product(L, ctx, n):
     Gx = O.kernel_matrix(inst.Q[rows], inst.scale, inst.Q) @ x + inst.lam * x[rows]
     w = host(L.laker_op_matvec(ctx, op, dev(x)))[rows]
     assert rel(w, Gx) < 1e-5
+
+
+def test_c1_stopping_index_five_seeds(L, ctx):
+    """The c1 configuration (n = 1024, d = 16, lambda = 1e-3, 3 Tx, N_r = 128,
+    tol 1e-8) on five seeds: the GPU's number of products lies within the
+    oracle's own envelope of it (plain run, six summation-order permutations,
+    six runs with per-apply noise at the measured difference between the
+    GPU's float64 apply and the oracle's dense Sigma^-1/2 r), widened by the
+    envelope's width.  Prints the distribution of GPU - oracle."""
+    from tests.gpu_util import dev, host, rel
+    cfg = synth.CONFIGS["c1"]
+    deltas = []
+    for seed in (1001, 1002, 1003, 1004, 1005):
+        inst = synth.make_instance(cfg["n"], cfg["d"], cfg["lam"], n_tx=cfg["n_tx"], seed=seed, grid=2)
+        n = inst.n
+        Z = synth.directions(n, synth.default_num_directions(n), seed)
+        A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+        Pd = O.inverse_sqrt(O.cccp_fit(O.random_directions(A, Z), 0.1,
+                                       O.shrinkage_rho(n, Z.shape[1], 0.1), 1e-8).Sigma)
+        op = L.laker_build_kernel(ctx, dev(inst.Q), inst.scale, inst.lam, L.FP64)
+        P = L.laker_fit_preconditioner(ctx, op, dev(Z))
+        alpha, info = L.laker_pcg_solve(ctx, op, P, dev(inst.y), cfg["tol"])
+        v = synth.random_vector(n, seed)
+        pv_err = rel(host(L.laker_precond_apply(ctx, P, dev(v))), Pd @ v)
+        env = tol_envelope(A, inst.y, Pd, cfg["tol"], p_rel=max(pv_err, 1e-15), seed=seed)
+        k0 = O.pcg(A, inst.y, Pd, cfg["tol"]).iterations
+        deltas.append(info["iterations"] - k0)
+        print(f"seed {seed}: GPU {info['iterations']}, oracle {k0}, envelope {env}, apply difference {pv_err:.1e}")
+        assert within_envelope(info["iterations"], env), (seed, info["iterations"], env)
+        assert O.relative_residual(A, host(alpha), inst.y) <= 1e-8 * 1.01
+    print("GPU - oracle products over the seeds:", deltas)
