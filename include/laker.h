@@ -51,8 +51,8 @@ typedef enum {
 } laker_precision;
 
 /* How the operator v -> (lambda I + G) v is evaluated.  FP64 operators are
- * materialised; BF16X3 operators are matrix-free; FP32 operators with
- * d <= 64 have both variants (the matrix-free one recomputes G with the
+ * materialised; BF16X3 operators are matrix-free; FP32 operators whose d
+ * rounds up to 16, 32 or 64 (d <= 32 or 49 <= d <= 64) have both variants (the matrix-free one recomputes G with the
  * split-bf16 tensor-core kernel, ~1e-6 relative), and LAKER_AUTO times one
  * product of each after the build and keeps the faster for this n (the
  * choice and both times are reported by laker_op_describe). */

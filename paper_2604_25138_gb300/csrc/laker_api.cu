@@ -157,7 +157,8 @@ laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int 
     // split-bf16 operators are matrix-free; float64 operators are materialised;
     // float32 operators (d <= 64, scale > 0) have both variants, and AUTO
     // times one product of each after the build and keeps the faster
-    const bool fp32_mf_ok = precision == LAKER_FP32 && d <= 64 && scale > 0.0;
+    const int dpad = (d + 15) / 16 * 16;   // the tensor-core kernels take dpad = 16, 32 or 64
+    const bool fp32_mf_ok = precision == LAKER_FP32 && (dpad == 16 || dpad == 32 || dpad == 64) && scale > 0.0;
     const bool autotune = variant == LAKER_AUTO && fp32_mf_ok;
     if (variant == LAKER_AUTO)
         variant = (precision == LAKER_BF16X3) ? LAKER_MATRIX_FREE : LAKER_MATERIALISED;
@@ -165,11 +166,12 @@ laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int 
     if (precision == LAKER_FP64 && variant == LAKER_MATRIX_FREE)
         return set_error(ctx, LAKER_ERR_UNSUPPORTED, "float64 operators are materialised only");
     if (precision == LAKER_FP32 && variant == LAKER_MATRIX_FREE && !fp32_mf_ok)
-        return set_error(ctx, LAKER_ERR_UNSUPPORTED, "the matrix-free float32 operator needs d <= 64 and scale > 0");
+        return set_error(ctx, LAKER_ERR_UNSUPPORTED, "the matrix-free float32 operator needs d <= 32 or 49 <= d <= 64, and scale > 0");
     if ((st = scan_finite(ctx, Q, n * d)) != LAKER_OK) return st;
     laker_op* op = new (std::nothrow) laker_op();
     if (!op) return LAKER_ERR_OOM;
     op->ctx = ctx;
+    op->device = ctx->device;
     op->n = n;
     op->d = d;
     op->scale = scale;
@@ -220,9 +222,11 @@ laker_status laker_op_describe(const laker_op* op, int* precision, int* variant,
     return LAKER_OK;
 }
 
+// Destroy calls do not touch the context, which the caller may have destroyed
+// first; a handle keeps its own device.
 laker_status laker_op_destroy(laker_op* op) {
     if (!op) return LAKER_ERR_ARG;
-    cudaSetDevice(op->ctx->device);
+    if (cudaSetDevice(op->device) != cudaSuccess) cudaGetLastError();
     free_op(op);
     return LAKER_OK;
 }
@@ -270,6 +274,7 @@ laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const 
     laker_precond* P = new (std::nothrow) laker_precond();
     if (!P) return LAKER_ERR_OOM;
     P->ctx = ctx;
+    P->device = ctx->device;
     P->use32 = op->precision != LAKER_FP64;
     st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info);
     if (st != LAKER_OK) { free_precond(P); return st; }
@@ -293,6 +298,7 @@ laker_status laker_fit_preconditioner_seeded(laker_ctx* ctx, const laker_op* op,
     laker_precond* P = new (std::nothrow) laker_precond();
     if (!P) { cudaFree(Z); return LAKER_ERR_OOM; }
     P->ctx = ctx;
+    P->device = ctx->device;
     P->use32 = op->precision != LAKER_FP64;
     st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info);
     cudaStreamSynchronize(ctx->stream);
@@ -319,6 +325,7 @@ laker_status laker_fit_preconditioner_learned(laker_ctx* ctx, const laker_op* op
     laker_precond* P = new (std::nothrow) laker_precond();
     if (!P) return LAKER_ERR_OOM;
     P->ctx = ctx;
+    P->device = ctx->device;
     P->use32 = op->precision != LAKER_FP64;
     st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info, net, X, mode);
     if (st != LAKER_OK) { free_precond(P); return st; }
@@ -343,6 +350,7 @@ laker_status laker_precond_jacobi(laker_ctx* ctx, const laker_op* op, laker_prec
     laker_precond* P = new (std::nothrow) laker_precond();
     if (!P) return LAKER_ERR_OOM;
     P->ctx = ctx;
+    P->device = ctx->device;
     P->kind = PRECOND_JACOBI;
     P->n = op->n;
     if ((st = lk_malloc(ctx, (void**)&P->dinv, (size_t)op->n * sizeof(double))) != LAKER_OK) { free_precond(P); return st; }
@@ -356,7 +364,7 @@ laker_status laker_precond_jacobi(laker_ctx* ctx, const laker_op* op, laker_prec
 
 laker_status laker_precond_destroy(laker_precond* P) {
     if (!P) return LAKER_ERR_ARG;
-    cudaSetDevice(P->ctx->device);
+    if (cudaSetDevice(P->device) != cudaSuccess) cudaGetLastError();
     free_precond(P);
     return LAKER_OK;
 }

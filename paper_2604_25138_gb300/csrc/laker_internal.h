@@ -46,6 +46,7 @@ struct laker_ctx {
 
 struct laker_op {
     laker_ctx* ctx = nullptr;
+    int device = 0;           // the context's device, kept for destroy
     int64_t n = 0;
     int d = 0;
     int dpad = 0;             // d rounded up to a multiple of 16 (bf16 operands)
@@ -76,6 +77,7 @@ enum PrecondKind { PRECOND_IDENTITY = 0, PRECOND_JACOBI = 1, PRECOND_CCCP = 2 };
 
 struct laker_precond {
     laker_ctx* ctx = nullptr;
+    int device = 0;           // the context's device, kept for destroy
     int kind = PRECOND_IDENTITY;
     int64_t n = 0;
     int n_r = 0;
