@@ -47,6 +47,9 @@ SINGLE = {
                n=65536, d=64, lam=1e-4, n_tx=8, layout="uniform", grid=512, tol=1e-6, refine_every=20, seed=3000),
     "c2": dict(name="single instance, n=16384 (70% uniform, 30% in 5 blobs), d=32, lambda=1e-4, 8 Tx, 512x512 grid",
                n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6, refine_every=20, seed=2000),
+    "c1": dict(name="plain method in float64: single instance, n=1024 uniform, d=16, lambda=1e-3, 3 Tx, 64x64 grid",
+               n=1024, d=16, lam=1e-3, n_tx=3, layout="uniform", grid=64, tol=1e-8, refine_every=0, seed=1000,
+               precision="FP64"),
 }
 # the bounded oracle sample timed on the host cores: the same generator as the
 # workload at n = 2048 (the dense oracle's CCCP costs O(n^3) per iteration:
@@ -57,6 +60,7 @@ CPU_SAMPLE_GRID = 64
 # the current kernel at the workload's size, or None
 MF_TRAFFIC_BYTES = None
 SFU_EX2_PER_CLK_PER_SM = 32   # ex2.approx results per clock per SM (micro-benchmarked on GB300)
+FP64_NOMINAL_TFLOPS = 1.25    # dense float64 rate of GB300 (nominal)
 
 
 def workload(cfg: dict, seed: int, n: int | None = None, grid: int | None = None):
@@ -196,7 +200,9 @@ def run_ours(args):
             op = None
         return alpha, fmap, info, P.info, op
 
-    mixed = dict(precision=L.BF16X3, refine=cfg["refine_every"], tol=cfg["tol"])
+    prec_name = cfg.get("precision", "BF16X3")
+    fp64_only = prec_name == "FP64"
+    mixed = dict(precision=getattr(L, prec_name), refine=cfg["refine_every"], tol=cfg["tol"])
     for _ in range(args.warmup):
         step(Q, y, Z, Qg, **mixed)
     torch.cuda.synchronize()
@@ -252,31 +258,58 @@ def run_ours(args):
     # the tiles are implementation work and are not counted.  The time is that
     # of the whole product as PCG issues it (preparation, tensor-core kernel,
     # finish).
-    op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.BF16X3)
     x = to_dev(synth.random_vector(n, 1))
-    prod_ms = L.laker_op_time_product(ctx, op, x, reps=20)
-    main_ms = L.laker_op_time_operator(ctx, op, x, reps=20)
-    op.close()
-    pairs = n * (n + 1) / 2.0
-    flops = pairs * 3 * 2 * inst.d
-    bf16_peak, peak_kind = peaks_bf16()
-    sfu_peak = SFU_EX2_PER_CLK_PER_SM * 152 * 2.07e9
-    t_tensor = flops / (bf16_peak * 1e12)
-    t_sfu = pairs / sfu_peak
-    achieved = flops / (prod_ms * 1e-3) / 1e12
-    bound = "tensor" if t_tensor >= t_sfu else "sfu"
-    # the streamed float32 materialised product, for the variant choice per n
-    opm = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32)
-    mat_ms = L.laker_op_time_product(ctx, opm, x, reps=10)
-    opm.close()
     ldk = (n + 3) // 4 * 4
-    mat_gbs = (n * ldk * 4 + 3 * n * 8) / (mat_ms * 1e-3) / 1e9
     hbm, hbm_kind = peaks()
+    if fp64_only:
+        # the plain method: the float64 G (8 MiB at n = 1024, L2-resident) is
+        # streamed by the float64 product, bound by the float64 FMA rate
+        op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP64)
+        prod_ms = L.laker_op_time_product(ctx, op, x, reps=50)
+        op.close()
+        flops = 2.0 * n * n
+        achieved = flops / (prod_ms * 1e-3) / 1e12
+        roofline = {"kernel": "k_matvec_mat<double> (float64 G, L2-resident)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                    "peak_kind": "nominal dense float64 rate of GB300 (not in MEASURED_PEAKS.json)",
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "flops_per_product": flops, "ms_per_product": prod_ms,
+                    "note": "G fits in L2; the product is latency- and float64-bound, not an HBM stream"}
+        variant_cmp = None
+    else:
+        op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.BF16X3)
+        prod_ms = L.laker_op_time_product(ctx, op, x, reps=20)
+        main_ms = L.laker_op_time_operator(ctx, op, x, reps=20)
+        op.close()
+        pairs = n * (n + 1) / 2.0
+        flops = pairs * 3 * 2 * inst.d
+        bf16_peak, peak_kind = peaks_bf16()
+        sfu_peak = SFU_EX2_PER_CLK_PER_SM * 152 * 2.07e9
+        t_tensor = flops / (bf16_peak * 1e12)
+        t_sfu = pairs / sfu_peak
+        achieved = flops / (prod_ms * 1e-3) / 1e12
+        roofline = {"kernel": "matrix-free product: k_mf_prep + k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, row and "
+                              "column sums) + k_mf_finish",
+                    "bound": "tensor" if t_tensor >= t_sfu else "sfu", "achieved": achieved, "peak": bf16_peak,
+                    "peak_kind": peak_kind + " bf16 burst (kernel timed alone)", "unit": "TFLOP/s",
+                    "frac": achieved / bf16_peak, "traffic": MF_TRAFFIC_BYTES,
+                    "method_flops_per_product": flops, "unique_pairs": pairs,
+                    "ms_per_product": prod_ms, "ms_main_kernel": main_ms,
+                    "tensor_roof_ms": t_tensor * 1e3, "sfu_roof_ms": t_sfu * 1e3,
+                    "sfu_peak_ex2_per_s": sfu_peak,
+                    "frac_of_binding_roof": max(t_tensor, t_sfu) * 1e3 / prod_ms}
+        # the streamed float32 materialised product, for the variant choice per n
+        opm = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32, L.MATERIALISED)
+        mat_ms = L.laker_op_time_product(ctx, opm, x, reps=10)
+        opm.close()
+        mat_gbs = (n * ldk * 4 + 3 * n * 8) / (mat_ms * 1e-3) / 1e9
+        variant_cmp = {"ms_per_product": mat_ms, "achieved_gbs": mat_gbs, "peak_gbs": hbm, "peak_kind": hbm_kind,
+                       "frac": mat_gbs / hbm, "vs_matrix_free": mat_ms / prod_ms}
 
     # plain float64 path on the same instance (the paper's method in float64)
     plain = None
     accuracy = None
-    if args.plain_steps > 0:
+    if args.plain_steps > 0 and not fp64_only:
         torch.cuda.synchronize()
         p0 = time.perf_counter()
         for k in range(args.plain_steps):
@@ -308,14 +341,17 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 split (hi/lo) logits, f32 exp and sums, f64 scalars and residual",
+        "vs_baseline": None,
+        "dtype": "f64" if fp64_only else "bf16 split (hi/lo) logits, f32 exp and sums, f64 scalars and residual",
         "data": "synthetic",
         "config": {"workload": cfg["name"] + ", N_r=%d, tol %g true residual" % (n_r, cfg["tol"]),
                    "n": n, "d": inst.d, "lambda": inst.lam, "n_r": n_r, "grid": cfg["grid"] ** 2,
-                   "operator": "matrix-free tcgen05 split-bf16 logits + ex2, float64-accurate residual every "
-                               "%d products" % cfg["refine_every"],
-                   "l2": "working set larger than L2 (129 MB): directions %.1f GB, float32 pair of G %.1f GB"
-                         % (n * n_r * 8 / 1e9, n * ldk * 8 / 1e9),
+                   "operator": ("materialised float64 G" if fp64_only else
+                                "matrix-free tcgen05 split-bf16 logits + ex2, float64-accurate residual every "
+                                "%d products from the packed upper-triangular float32 pair" % cfg["refine_every"]),
+                   "l2": ("working set fits in L2 (G: %.1f MB float64)" % (n * ldk * 8 / 1e6) if fp64_only else
+                          "working set larger than L2 (129 MB): directions %.2f GB, packed float32 pair %.1f GB"
+                          % (n * n_r * 8 / 1e9, n * (n + 1) / 2 * 8 / 1e9)),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "phases_ms_last_step": phases[-1] if phases else None,
         "solve": {"iterations": info["iterations"], "true_residuals": info["true_residuals"],
@@ -326,19 +362,9 @@ def run_ours(args):
         "accuracy_vs_fp64": accuracy,
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"kernel": "matrix-free product: k_mf_prep + k_mf_bf16x3 (tcgen05 split-bf16 logits, ex2, "
-                               "row and column sums) + k_mf_finish",
-                     "bound": bound, "achieved": achieved, "peak": bf16_peak,
-                     "peak_kind": peak_kind + " bf16 burst (kernel timed alone)", "unit": "TFLOP/s",
-                     "frac": achieved / bf16_peak, "traffic": MF_TRAFFIC_BYTES,
-                     "method_flops_per_product": flops, "unique_pairs": pairs,
-                     "ms_per_product": prod_ms, "ms_main_kernel": main_ms,
-                     "tensor_roof_ms": t_tensor * 1e3, "sfu_roof_ms": t_sfu * 1e3,
-                     "sfu_peak_ex2_per_s": sfu_peak,
-                     "frac_of_binding_roof": max(t_tensor, t_sfu) * 1e3 / prod_ms},
-        "materialised_fp32_matvec": {"ms_per_product": mat_ms, "achieved_gbs": mat_gbs, "peak_gbs": hbm,
-                                     "peak_kind": hbm_kind, "frac": mat_gbs / hbm,
-                                     "vs_matrix_free": mat_ms / prod_ms},
+        "roofline": roofline,
+        "materialised_fp32_matvec": variant_cmp,
+        "ms_per_pcg_product": (phases[-1]["solve"] / max(1, info["iterations"])) if phases else None,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -671,6 +697,153 @@ def run_variants(args):
                       "peak_hbm_gbs": peaks()[0]}))
 
 
+def run_combined(args):
+    """The target comparison: the mixed, batched, learned-preconditioner form
+    against plain float64 PCG on the same GB300, in solves/s at a true
+    relative residual of 1e-6.
+
+    A set network is trained once, outside the timed region, on the method's
+    own CCCP fits of training instances (n uniform in [1024, 4096], d = 32,
+    lambda log-uniform in [1e-5, 1e-2], 1-8 Tx).  A timed step takes
+    `--combined-count` held-out instances of the same distribution through:
+    * combined: float32 operators, the network's prediction used as Sigma_*
+      (no CCCP iteration), one persistent batched mixed PCG launch over all
+      instances; an instance that has not converged after `--combined-cap`
+      products falls back to a CCCP fit and a single solve (charged to the
+      step);
+    * mixed batched CCCP: the same, with CCCP fits;
+    * plain float64: float64 operator, CCCP fit and PCG per instance, one at
+      a time (the paper's method as printed)."""
+    import torch
+
+    from paper_2604_25138_gb300 import build
+    from paper_2604_25138_gb300 import laker as L
+    from paper_2604_25138_gb300 import learned
+
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = L.Context(0)
+    rng = np.random.default_rng(6006)
+
+    def draw(k0, count):
+        out = []
+        for k in range(count):
+            n = int(rng.integers(1024, 4097))
+            lam = float(10 ** rng.uniform(-5, -2))
+            out.append(synth.make_instance(n, 32, lam, n_tx=int(rng.integers(1, 9)), seed=k0 + k, grid=2))
+        return out
+
+    t0 = time.perf_counter()
+    train_set = [learned.fit_example(ctx, inst, seed=inst.seed) for inst in draw(90000, args.learned_train)]
+    net = L.SetNet(ctx, 32 + 3, 256, 64, seed=6)
+    losses = learned.train(ctx, net, train_set, steps=args.learned_steps, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    insts = draw(95000, args.combined_count)
+    tol = 1e-6
+
+    def dev(x):
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+    ins = [(dev(i.Q), dev(i.y), dev(synth.directions(i.n, synth.default_num_directions(i.n), i.seed)),
+            learned.instance_inputs(ctx, i)) for i in insts]
+
+    phase_ms = {}
+
+    def mark(name, t0):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        phase_ms[name] = 1e3 * (t1 - t0)
+        return t1
+
+    def combined_step(mode):
+        ops, precs = [], []
+        t = time.perf_counter()
+        for inst, (Q, y, Z, X) in zip(insts, ins):
+            ops.append(L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP32, L.MATERIALISED))
+        t = mark("build", t)
+        for op, (Q, y, Z, X) in zip(ops, ins):
+            if mode == "learned":
+                precs.append(L.laker_fit_preconditioner_learned(ctx, op, Z, net, X, mode=1))
+            else:
+                precs.append(L.laker_fit_preconditioner(ctx, op, Z))
+        t = mark("precondition", t)
+        items = [(op, P, y, None) for op, P, (_, y, _, _) in zip(ops, precs, ins)]
+        alphas, infos, _ = L.laker_pcg_solve_batched(ctx, items, tol, max_iter=args.combined_cap, refine_every=20,
+                                                    allow_maxiter=True)
+        t = mark("batched_solve", t)
+        fallback = 0
+        if mode == "learned":
+            for k, f in enumerate(infos):
+                if f["converged"] != 1:
+                    fallback += 1
+                    P = L.laker_fit_preconditioner(ctx, ops[k], ins[k][2])
+                    _, f2 = L.laker_pcg_solve(ctx, ops[k], P, ins[k][1], tol, max_iter=40000, refine_every=20)
+                    infos[k] = f2
+                    P.close()
+        worst = max(f["rel_res_true"] for f in infos)
+        for P in precs:
+            P.close()
+        for op in ops:
+            op.close()
+        mark("fallback_and_release", t)
+        return infos, fallback, worst, dict(phase_ms)
+
+    def plain_step():
+        worst, its = 0.0, []
+        for inst, (Q, y, Z, _) in zip(insts, ins):
+            op = L.laker_build_kernel(ctx, Q, inst.scale, inst.lam, L.FP64)
+            P = L.laker_fit_preconditioner(ctx, op, Z)
+            _, f = L.laker_pcg_solve(ctx, op, P, y, tol, max_iter=40000)
+            worst = max(worst, f["rel_res_true"])
+            its.append(f["iterations"])
+            P.close()
+            op.close()
+        return its, worst
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps, out
+
+    for _ in range(max(1, args.warmup)):
+        combined_step("learned")
+        combined_step("cccp")
+    count = len(insts)
+    launches0 = ctx.launches()
+    with ClockSampler(0) as clk:
+        s_l, (inf_l, fb, worst_l, ph_l) = timed(lambda: combined_step("learned"), args.steps)
+    launches = ctx.launches() - launches0
+    s_c, (inf_c, _, worst_c, ph_c) = timed(lambda: combined_step("cccp"), 1)
+    s_p, (its_p, worst_p) = timed(plain_step, 1)
+    line = {
+        "metric": "solves/s at true rel-res 1e-6: mixed + batched + learned preconditioner vs plain FP64 PCG",
+        "value": count / s_l, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": s_l * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 operator + f64 scalars/residual, bf16 set network", "data": "synthetic",
+        "config": {"workload": "combined form: %d held-out instances, n uniform in [1024, 4096], d = 32, lambda "
+                               "log-uniform in [1e-5, 1e-2], 1-8 Tx; network trained on %d CCCP fits (%d Adam steps, "
+                               "%.1f s, outside the timed step)" % (count, args.learned_train, args.learned_steps,
+                                                                     train_s),
+                   "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:]))},
+        "combined": {"solves_per_s": count / s_l, "fallbacks": fb, "worst_rel_res_true": worst_l,
+                     "pcg_products_mean": float(np.mean([f["iterations"] for f in inf_l])),
+                     "phases_ms_last_step": ph_l},
+        "mixed_batched_cccp": {"solves_per_s": count / s_c, "worst_rel_res_true": worst_c,
+                               "pcg_products_mean": float(np.mean([f["iterations"] for f in inf_c])),
+                               "phases_ms": ph_c},
+        "plain_fp64": {"solves_per_s": count / s_p, "worst_rel_res_true": worst_p,
+                       "pcg_products_mean": float(np.mean(its_p))},
+        "speedup_vs_plain_fp64": s_p / s_l,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 # ---------------------------------------------------------------------------
 # The FP64 oracle on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
@@ -765,13 +938,15 @@ def main():
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[50, 200, 500, 1000, 2000, 4000, 8000])
     ap.add_argument("--gd-steps", type=int, default=2000)
     ap.add_argument("--variant-sizes", type=int, nargs="+", default=[512, 1024, 2048, 4096, 8192, 16384, 32768])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "batched", "learned", "sweep", "variants"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "batched", "learned", "sweep", "variants", "combined"],
                     help="c3: the precision-form instance n=65536, d=64 (the headline line); c2: the n=16384 "
                          "instance; batched: 256 instances; learned: the set-network preconditioner")
     ap.add_argument("--learned-train", type=int, default=256)
     ap.add_argument("--learned-test", type=int, default=32)
     ap.add_argument("--learned-big", type=int, default=4)
     ap.add_argument("--learned-steps", type=int, default=2000)
+    ap.add_argument("--combined-count", type=int, default=96)
+    ap.add_argument("--combined-cap", type=int, default=4000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -783,6 +958,8 @@ def main():
         run_sweep(args)
     elif args.workload == "variants":
         run_variants(args)
+    elif args.workload == "combined":
+        run_combined(args)
     else:
         run_ours(args)
 
