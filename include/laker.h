@@ -84,6 +84,7 @@ typedef struct {
     double rel_res;      /* |r|/|y| of the recursive residual at exit */
     double rel_res_true; /* |y - (lambda I + G) alpha| / |y| (float64 operator) */
     int status;          /* laker_status of the solve */
+    int restarts;        /* mixed single solves: roll-backs of the replacement guard */
 } laker_solve_info;
 
 /* Context: binds a device and a CUDA stream (cudaStream_t passed as void*).
@@ -248,7 +249,16 @@ laker_status laker_precond_export(laker_ctx* ctx, const laker_precond* P, double
  *              whenever the recursive residual passes the test, r is replaced
  *              by y - (lambda I + G) alpha computed with the float64-accurate
  *              operator, and the stop test uses that true residual.  0 = never.
- * alpha (device, n) receives the last iterate, also on LAKER_ERR_MAXITER.
+ *              The replacements are guarded: the lowest true residual seen
+ *              is kept with its iterate; a replacement more than 30 times
+ *              above it, a product with p^T A p <= 0 or a non-finite
+ *              residual roll alpha back to it, restart the direction and
+ *              halve the interval (at least 4).  A roll-back at interval 4
+ *              ends the solve with LAKER_ERR_MAXITER ("stagnated": the
+ *              tolerance is below what the operator's accuracy lets the
+ *              solve reach).
+ * alpha (device, n) receives the last iterate, also on LAKER_ERR_MAXITER
+ *              (mixed forms: the iterate with the lowest true residual).
  */
 laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
                              const double* y, double* alpha, double tol, int max_iter,

@@ -760,6 +760,7 @@ laker_status pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item
             f.rel_res = s.yy > 0.0 ? std::sqrt(s.rr / s.yy) : 0.0;
             f.rel_res_true = s.yy > 0.0 ? std::sqrt(s.rr_true / s.yy) : 0.0;
             f.status = si;
+            f.restarts = 0;
         }
         if (done_ms) done_ms[i] = (s.t_done > hg.t0) ? (double)(s.t_done - hg.t0) * 1e-6 : 0.0;
         if (si == LAKER_ERR_BREAKDOWN) worst = si;

@@ -239,6 +239,7 @@ extern "C" laker_status laker_gd_solve(laker_ctx* ctx, const laker_op* op, const
         info->rel_res = yy > 0 ? std::sqrt(hs.rr / yy) : 0.0;
         info->rel_res_true = yy > 0 ? std::sqrt(rt / yy) : 0.0;
         info->status = result;
+        info->restarts = 0;
     }
     return result == LAKER_OK ? LAKER_OK : set_error(ctx, result, "gradient descent reached max_iter");
 }

@@ -19,7 +19,7 @@ struct PcgScalars {
     double yy;          // |y|^2
     double tol2yy;      // tol^2 |y|^2
     double rr_true;     // |y - A alpha|^2 at the last true-residual step
-    int converged;      // 0 running, 1 converged, 2 breakdown, 3 max iterations
+    int converged;      // 0 running, 1 converged, 2 breakdown, 3 max iterations, 4 stagnated
     int iters;          // operator products so far
     int need_true;      // the next true-residual step must run
     int true_count;     // true residuals computed
@@ -32,6 +32,15 @@ struct PcgScalars {
     int pad2;
     double R_ref;       // reference objective of the gap stop
     double gap_tol;     // > 0: stop once |R(alpha) - R_ref| <= gap_tol |R_ref|
+    // Guard of the mixed forms (residual replacement with an inexact operator)
+    double rr_best;     // lowest true |r|^2 seen at a replacement (HUGE_VAL before the first)
+    int interval;       // current replacement interval (starts at refine_every)
+    int since_true;     // products since the last replacement
+    int restarts;       // roll-backs to the best iterate
+    int guard_action;   // 1: save alpha, r as the best iterate; 2: restore them
+    int restart_dir;    // 1: the next direction is the preconditioned residual (beta = 0)
+    int breakdown;      // p^T A p <= 0 in a mixed solve: replace and roll back
+    int pad3, pad4;
 };
 
 struct laker_ctx {

@@ -358,7 +358,10 @@ __global__ void k_mf_prep(int64_t n, int64_t npad, const double* __restrict__ pi
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npad) return;
     if (i >= n) { pf[i] = 0.f; return; }
-    const double p = fuse ? fma(sc->beta, pin[i], z[i]) : pin[i];
+    // beta = 0 starts a new direction; p_old is not read (it may hold what a
+    // broken-down step left)
+    const double b = fuse ? sc->beta : 0.0;
+    const double p = !fuse ? pin[i] : (b == 0.0 ? z[i] : fma(b, pin[i], z[i]));
     if (fuse) pout[i] = p;
     pf[i] = (float)p;
 }
@@ -428,8 +431,13 @@ k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ row
         const double pAp = lk::sum_partials(partials, gridDim.x * gridDim.y, red);
         if (threadIdx.x == 0) {
             sc->pAp = pAp;
-            if (*(volatile const int*)err != 0 || !(pAp > 0.0) || !isfinite(pAp)) {
+            if (*(volatile const int*)err != 0) {
                 sc->converged = 2;
+                sc->delta = 0.0;
+            } else if (!(pAp > 0.0) || !isfinite(pAp)) {
+                // mixed forms: the guard replaces the residual and rolls back
+                if (sc->refine_every > 0) sc->breakdown = 1;
+                else sc->converged = 2;
                 sc->delta = 0.0;
             } else {
                 sc->delta = sc->rz / pAp;

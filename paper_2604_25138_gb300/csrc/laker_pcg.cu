@@ -128,7 +128,7 @@ k_matvec_mat(const T* __restrict__ K, int64_t ldk, int64_t n, double lambda, int
     double pw = 0.0;
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         const int64_t gi = r0 + i;
-        const double pi = fuse ? fma(beta, pin[gi], z[gi]) : pin[gi];
+        const double pi = !fuse ? pin[gi] : (beta == 0.0 ? z[gi] : fma(beta, pin[gi], z[gi]));
         const double wi = fma(lambda, pi, acc[i]);
         w[gi] = wi;
         if (fuse) pout[gi] = pi;
@@ -142,7 +142,9 @@ k_matvec_mat(const T* __restrict__ K, int64_t ldk, int64_t n, double lambda, int
         if (threadIdx.x == 0) {
             sc->pAp = pAp;
             if (!(pAp > 0.0) || !isfinite(pAp)) {
-                sc->converged = 2;
+                // mixed forms: the guard replaces the residual and rolls back
+                if (sc->refine_every > 0) sc->breakdown = 1;
+                else sc->converged = 2;
                 sc->delta = 0.0;
             } else {
                 sc->delta = sc->rz / pAp;
@@ -256,7 +258,8 @@ struct PrecView {
 // INIT: alpha = 0, r = y, p = 0, |y|^2.
 __global__ void __launch_bounds__(VEC_THREADS)
 k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, double* __restrict__ r,
-           double* __restrict__ p0, PcgScalars* sc, double* __restrict__ partials, double tol) {
+           double* __restrict__ p0, double* __restrict__ abest, double* __restrict__ rbest, PcgScalars* sc,
+           double* __restrict__ partials, double tol) {
     __shared__ double red[VEC_THREADS / 32];
     int64_t r0, r1;
     row_range(n, r0, r1);
@@ -266,6 +269,8 @@ k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, 
         alpha[i] = 0.0;
         r[i] = yi;
         p0[i] = 0.0;
+        abest[i] = 0.0;   // the guard's fallback before its first replacement: alpha = 0
+        rbest[i] = yi;
         yy = fma(yi, yi, yy);
     }
     yy = lk::block_sum(yy, red);
@@ -342,22 +347,51 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
                 trace[4 * (it - 1) + 2] = R;
             }
             const bool small = tot <= sc->tol2yy;
-            if (!isfinite(tot)) {
+            if (sc->refine_every > 0) {
+                // mixed forms: a non-finite recursive residual or a breakdown
+                // is handled by the guard at the replacement it forces
+                sc->since_true += 1;
+                if (!isfinite(tot)) sc->breakdown = 1;
+                if (isfinite(tot) && gap && fabs(R - sc->R_ref) <= sc->gap_tol * fabs(sc->R_ref))
+                    sc->converged = 1;   // objective gap reached (Eq. iterations, TAR.TOL)
+                else if (small || sc->breakdown || sc->since_true >= sc->interval || it >= sc->max_iter)
+                    sc->need_true = 1;
+            } else if (!isfinite(tot)) {
                 sc->converged = 2;
             } else if (gap && fabs(R - sc->R_ref) <= sc->gap_tol * fabs(sc->R_ref)) {
                 sc->converged = 1;   // objective gap reached (Eq. iterations, TAR.TOL)
-            } else if (sc->refine_every == 0) {
-                if (small) sc->converged = 1;
-                else if (it >= sc->max_iter) sc->converged = 3;
-            } else {
-                if (small || (it % sc->refine_every) == 0 || it >= sc->max_iter) sc->need_true = 1;
+            } else if (small) {
+                sc->converged = 1;
+            } else if (it >= sc->max_iter) {
+                sc->converged = 3;
             }
             sc->ticket[2] = 0;
         }
     }
 }
 
-// TR2: r = y - w2 with w2 = (lambda I + G) alpha; stop test on the true residual.
+// TR2: r = y - w2 with w2 = (lambda I + G) alpha; stop test on the true
+// residual, and the guard of the mixed forms.
+//
+// Between replacements the recursion runs on the inexact operator A~.  Where
+// A~ is within its own rounding of losing definiteness (split-bf16 products
+// at n = 65536, lambda = 1e-4: the float32 accumulation and ex2.approx errors
+// are of order lambda along the bottom of the spectrum), long intervals let
+// CG build directions along which p^T A~ p is wrong or <= 0, and the true
+// residual grows without bound: measured, a replacement every 30 products
+// diverged on that instance after reaching 1.2e-6, every 20 converged.  The
+// recursive residual itself stays within ~1e-3 of the true one at every
+// replacement, so the guard watches the true residual: the lowest one seen is
+// saved with its iterate; a replacement 30 times above it (healthy solves stay
+// within ~3 times of their running best once past the first replacement), a
+// breakdown p^T A~ p <= 0 or a non-finite residual roll back to the saved
+// iterate, restart the direction and halve the interval.  At the smallest
+// interval a further roll-back ends the solve (stagnation).  (The true energy
+// phi(alpha), exact CG's monotone quantity, cannot serve: near convergence its
+// changes are below the cancellation of y^T alpha in float64.)
+constexpr int GUARD_MIN_INTERVAL = 4;
+constexpr double GUARD_GROWTH2 = 900.0;   // (30x)^2 in |r|^2
+
 __global__ void __launch_bounds__(VEC_THREADS)
 k_true_residual(int64_t n, const double* __restrict__ y, const double* __restrict__ w2, double* __restrict__ r,
                 PcgScalars* sc, double* __restrict__ partials) {
@@ -380,10 +414,61 @@ k_true_residual(int64_t n, const double* __restrict__ y, const double* __restric
             sc->rr_true = tot;
             sc->true_count += 1;
             sc->need_true = 0;
-            if (!isfinite(tot)) sc->converged = 2;
-            else if (tot <= sc->tol2yy) sc->converged = 1;
-            else if (sc->iters >= sc->max_iter) sc->converged = 3;
+            sc->since_true = 0;
+            const bool bad = !isfinite(tot);
+            int action = 0;
+            if (!bad && tot <= sc->tol2yy) {
+                sc->converged = 1;
+            } else if (!bad && tot < sc->rr_best) {
+                sc->rr_best = tot;
+                action = 1;
+                if (sc->breakdown) sc->restart_dir = 1;   // keep the iterate, drop the direction
+            } else if (bad || sc->breakdown || tot > GUARD_GROWTH2 * sc->rr_best) {
+                action = 2;
+                if (sc->interval <= GUARD_MIN_INTERVAL) {
+                    sc->converged = 4;   // stagnated: the saved iterate is returned
+                } else {
+                    sc->interval = max(GUARD_MIN_INTERVAL, sc->interval / 2);
+                    sc->restarts += 1;
+                    sc->restart_dir = 1;
+                }
+            }
+            sc->breakdown = 0;
+            if (sc->converged == 0 && sc->iters >= sc->max_iter) {
+                sc->converged = 3;
+                if (action == 0) action = 2;   // return the lowest-residual iterate
+            }
+            sc->guard_action = action;
             sc->ticket[3] = 0;
+        }
+    }
+}
+
+// Guard copies: action 1 saves (alpha, r) as the best iterate, action 2
+// restores them.  Every block reads the action before it counts itself done,
+// so the last block to finish can clear it for the next replacement.
+__global__ void __launch_bounds__(VEC_THREADS)
+k_pcg_guard(int64_t n, double* __restrict__ alpha, double* __restrict__ r, double* __restrict__ abest,
+            double* __restrict__ rbest, PcgScalars* sc) {
+    const int action = *(volatile const int*)&sc->guard_action;
+    if (action == 0) return;
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    if (action == 1) {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            abest[i] = alpha[i];
+            rbest[i] = r[i];
+        }
+    } else {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            alpha[i] = abest[i];
+            r[i] = rbest[i];
+        }
+    }
+    if (lk::last_block(&sc->ticket[6])) {
+        if (threadIdx.x == 0) {
+            sc->guard_action = 0;
+            sc->ticket[6] = 0;
         }
     }
 }
@@ -585,7 +670,8 @@ k_precond(int64_t n, const double* __restrict__ r, double* __restrict__ z, PcgSc
             const double old = sc->rz;
             if (!isfinite(tot) || tot < 0.0) sc->converged = 2;
             else if (tot == 0.0) sc->converged = 1;
-            sc->beta = (old > 0.0) ? tot / old : 0.0;
+            sc->beta = (old > 0.0 && sc->restart_dir == 0) ? tot / old : 0.0;
+            sc->restart_dir = 0;
             sc->rz = tot;
             const int it = sc->iters;
             if (sc->trace && it >= 1 && it <= sc->trace_cap) sc->trace[4 * (it - 1) + 3] = sc->beta;
@@ -621,7 +707,7 @@ k_resid_norm(int64_t n, const double* __restrict__ y, const double* __restrict__
 // Host side
 // ---------------------------------------------------------------------------
 struct Workspace {
-    double *r, *z, *p[2], *w, *w2, *partials;
+    double *r, *z, *p[2], *w, *w2, *abest, *rbest, *partials;
     void* t;
     PcgScalars* sc;
     unsigned int* ticket;
@@ -725,9 +811,9 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
     ws.mv_blocks = mv_blocks_for(ctx, n);
     laker_status st;
     double* base = nullptr;
-    if ((st = lk_malloc(ctx, (void**)&base, (size_t)6 * n * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&base, (size_t)8 * n * sizeof(double))) != LAKER_OK) return st;
     ws.r = base; ws.z = base + n; ws.p[0] = base + 2 * n; ws.p[1] = base + 3 * n; ws.w = base + 4 * n;
-    ws.w2 = base + 5 * n;
+    ws.w2 = base + 5 * n; ws.abest = base + 6 * n; ws.rbest = base + 7 * n;
     // per-block partials of any of the kernels (the matrix-free finish runs one block per 128 rows)
     const int64_t nb = std::max<int64_t>(8 * ctx->num_sms + 8, 4 * ((n + 127) / 128) + 8);
     if ((st = lk_malloc(ctx, (void**)&ws.partials, (size_t)nb * sizeof(double))) != LAKER_OK) return st;
@@ -772,6 +858,8 @@ laker_status enqueue_iteration(laker_ctx* ctx, const laker_op* op, const PrecVie
                     : launch_mv_df(ctx, op, alpha, ws.w2, ws.sc, GATE_TRUE, ws.mv_blocks);
         if (st != LAKER_OK) return st;
         k_true_residual<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, ws.w2, ws.r, ws.sc, ws.partials);
+        LK_LAUNCHED(ctx);
+        k_pcg_guard<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, alpha, ws.r, ws.abest, ws.rbest, ws.sc);
         LK_LAUNCHED(ctx);
     }
     if ((st = launch_utr<PT>(ctx, n, pv, ws.r, (PT*)ws.t, ws.sc, GATE_RUNNING)) != LAKER_OK) return st;
@@ -921,6 +1009,8 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     PcgScalars init{};
     init.max_iter = max_iter;
     init.refine_every = mixed ? refine_every : 0;
+    init.interval = init.refine_every;
+    init.rr_best = HUGE_VAL;   // the first replacement sets it
     init.R_ref = R_ref;
     init.gap_tol = gap_tol;
     struct TraceBuf {
@@ -940,7 +1030,8 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     LK_CUDA(ctx, cudaMemcpyAsync(ws.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
 
     auto run_init = [&]() -> laker_status {
-        k_pcg_init<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, alpha, ws.r, ws.p[0], ws.sc, ws.partials, tol);
+        k_pcg_init<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, alpha, ws.r, ws.p[0], ws.abest, ws.rbest,
+                                                                   ws.sc, ws.partials, tol);
         LK_LAUNCHED(ctx);
         laker_status s2;
         if (use32) {
@@ -1019,8 +1110,12 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
         info->rel_res = out.yy > 0 ? std::sqrt(out.rr / out.yy) : 0.0;
         info->rel_res_true = out.yy > 0 ? std::sqrt(out.rr_true / out.yy) : 0.0;
         info->status = result;
+        info->restarts = out.restarts;
     }
     if (result != LAKER_OK)
-        return set_error(ctx, result, result == LAKER_ERR_BREAKDOWN ? "PCG breakdown" : "PCG reached max_iter");
+        return set_error(ctx, result, result == LAKER_ERR_BREAKDOWN ? "PCG breakdown"
+                                      : out.converged == 4 ? "mixed PCG stagnated at the operator's accuracy floor "
+                                                             "(the lowest-residual iterate is returned)"
+                                                           : "PCG reached max_iter");
     return LAKER_OK;
 }

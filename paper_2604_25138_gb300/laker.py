@@ -39,7 +39,8 @@ class FitInfo(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("true_residuals", ctypes.c_int), ("converged", ctypes.c_int),
-                ("rel_res", ctypes.c_double), ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int)]
+                ("rel_res", ctypes.c_double), ("rel_res_true", ctypes.c_double), ("status", ctypes.c_int),
+                ("restarts", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
