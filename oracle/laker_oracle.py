@@ -26,6 +26,9 @@ Paper map (arXiv 2604.25138):
 * Sec. V-A, Eqs. (simu-R-definition, residual, objective-gap,
   prediction-discrepancy, rmse, nmse): evaluation metrics.
 * Sec. V-A, numerical-layer baselines: gradient descent on R(alpha).
+* Sec. VI (future work: measurements arriving sequentially): the streaming
+  update's warm starts, ``pcg(alpha0=...)`` and ``warm_sigma0`` for
+  ``cccp_fit(Sigma0=...)``.
 * oracle/philox.py: the counter-based generator behind the device-drawn
   random directions (Philox4x32-10, Salmon et al. 2011).
 
@@ -166,6 +169,16 @@ def cccp_fit(Ubar: np.ndarray, gamma: float, rho: float, eps: float,
     return CCCPResult(Sigma=Sigma, iterations=t, converged=converged, history=hist, rho=rho)
 
 
+def warm_sigma0(Ubar: np.ndarray, c: float, D: np.ndarray) -> np.ndarray:
+    """Start of a warm-started CCCP (the streaming update): a previous fit's
+    Sigma_* = c I + sum_k D_k u_k u_k^T carried to the current normalised
+    directions u_k, Sigma_0 = (c I + Ubar diag(D) Ubar^T) scaled to trace n
+    like every CCCP iterate (Eq. kernel_shrinkage_cccp_normalization)."""
+    n = Ubar.shape[0]
+    S = c * np.eye(n) + (Ubar * np.asarray(D, dtype=np.float64)) @ Ubar.T
+    return S / (np.trace(S) / n)
+
+
 def inverse_sqrt(Sigma: np.ndarray) -> np.ndarray:
     """P = Sigma^(-1/2)  (Eq. preconditioner-Sigmma), by a symmetric
     eigendecomposition Sigma = V diag(w) V^T, P = V diag(w^-1/2) V^T."""
@@ -191,7 +204,7 @@ class PCGResult:
 
 
 def pcg(A: np.ndarray, y: np.ndarray, P: np.ndarray | None, tol: float,
-        max_iter: int = 100000, callback=None) -> PCGResult:
+        max_iter: int = 100000, callback=None, alpha0: np.ndarray | None = None) -> PCGResult:
     """Preconditioned CG exactly in the order of Algorithm 1:
 
         alpha^0 = 0, r^0 = y, theta^0 = P r^0, p^0 = theta^0
@@ -206,17 +219,28 @@ def pcg(A: np.ndarray, y: np.ndarray, P: np.ndarray | None, tol: float,
 
     P = None means the identity (plain CG).  ``callback(k, alpha)``, if given,
     sees each iterate alpha^k (k = 1, 2, ...); it changes no arithmetic, and a
-    true return value ends the iteration there."""
+    true return value ends the iteration there.
+
+    ``alpha0`` (the streaming update's warm start, the paper's future work of
+    Sec. VI): the iteration starts from alpha^0 = alpha0 with r^0 = y - A alpha0
+    instead of 0 and y, and a start with |r^0| / |y| <= tol returns at once
+    (0 iterations); the rest is unchanged."""
     y = np.asarray(y, dtype=np.float64)
     n = y.shape[0]
-    alpha = np.zeros(n)
-    r = y.copy()
+    if alpha0 is None:
+        alpha = np.zeros(n)
+        r = y.copy()
+    else:
+        alpha = np.array(alpha0, dtype=np.float64)
+        r = y - A @ alpha
     theta = r.copy() if P is None else P @ r
     p = theta.copy()
     rtheta = float(r @ theta)
     ny = float(np.linalg.norm(y))
     hist = []
     if ny == 0.0:
+        return PCGResult(alpha=alpha, iterations=0, converged=True, rel_res=hist)
+    if alpha0 is not None and float(np.linalg.norm(r)) / ny <= tol:
         return PCGResult(alpha=alpha, iterations=0, converged=True, rel_res=hist)
     for k in range(max_iter):
         Ap = A @ p

@@ -554,3 +554,105 @@ def test_philox_gaussian_directions_are_standard_normal():
         assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / m)
     np.testing.assert_array_equal(X.gaussian_directions(1234, 3, 5), Z.ravel()[:15].reshape(3, 5))
     assert not np.array_equal(X.gaussian_directions(1235, 3, 5), Z.ravel()[:15].reshape(3, 5))
+
+
+# --------------------------------------------------------------------------
+# Streaming update (Sec. VI, future work): warm-started PCG and CCCP
+# --------------------------------------------------------------------------
+
+def _spd_exact(n, seed):
+    """An SPD matrix with small-integer entries (exact in float64 and Fraction)."""
+    rng = np.random.default_rng(seed)
+    B = rng.integers(-3, 4, size=(n, n))
+    return (B @ B.T + n * np.eye(n, dtype=np.int64)).astype(np.int64)
+
+
+def test_warm_pcg_terminates_in_n_steps_from_any_start():
+    """CG from any start reaches the exact solution in at most n steps in
+    exact arithmetic (textbook): the solution is computed in Fraction
+    arithmetic by Gaussian elimination, and the oracle's warm start from a
+    far-off alpha0 must land on it after n = 4 steps (to rounding)."""
+    n = 4
+    Ai = _spd_exact(n, 3)
+    yi = np.array([3, -1, 2, 5])
+    # exact solution by Fraction Gaussian elimination
+    M = [[Fraction(int(Ai[i, j])) for j in range(n)] + [Fraction(int(yi[i]))] for i in range(n)]
+    for c in range(n):
+        piv = M[c][c]
+        for r in range(c + 1, n):
+            f = M[r][c] / piv
+            M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    x = [Fraction(0)] * n
+    for r in range(n - 1, -1, -1):
+        x[r] = (M[r][n] - sum(M[r][j] * x[j] for j in range(r + 1, n))) / M[r][r]
+    exact = np.array([float(v) for v in x])
+    A = Ai.astype(np.float64)
+    y = yi.astype(np.float64)
+    a0 = np.array([10.0, -7.0, 3.0, 0.5])
+    res = O.pcg(A, y, None, 0.0, max_iter=n, alpha0=a0)
+    np.testing.assert_allclose(res.alpha, exact, rtol=1e-12, atol=1e-12)
+    # and with a (diagonal) preconditioner as well
+    res = O.pcg(A, y, np.diag(1.0 / np.diag(A)), 0.0, max_iter=n, alpha0=a0)
+    np.testing.assert_allclose(res.alpha, exact, rtol=1e-12, atol=1e-12)
+
+
+def test_warm_pcg_from_the_solution_stops_before_any_product():
+    n = 6
+    A = _spd_exact(n, 5).astype(np.float64)
+    y = np.arange(1.0, n + 1.0)
+    a_star = np.linalg.solve(A, y)
+    res = O.pcg(A, y, None, 1e-10, alpha0=a_star)
+    assert res.iterations == 0 and res.converged
+    np.testing.assert_array_equal(res.alpha, a_star)
+    # a start that misses the tolerance does iterate
+    res = O.pcg(A, y, None, 1e-10, alpha0=a_star + 1e-3)
+    assert res.iterations >= 1 and res.converged
+
+
+def test_warm_pcg_is_cold_pcg_on_the_residual_system():
+    """PCG from alpha0 on A alpha = y is alpha0 plus PCG from 0 on
+    A e = y - A alpha0 (translation invariance of Krylov iterates): fails if
+    the warm start took r^0 = y, or kept alpha^0 = 0."""
+    inst = synth.make_instance(120, 8, 1e-2, seed=9, grid=2)
+    A = O.system_matrix(inst.Q, inst.scale, inst.lam)
+    P = np.diag(1.0 / np.sqrt(np.diag(A)))
+    a0 = synth.random_vector(120, 4)
+    for k in (1, 5, 17):
+        warm = O.pcg(A, inst.y, P, 0.0, max_iter=k, alpha0=a0).alpha
+        cold = O.pcg(A, inst.y - A @ a0, P, 0.0, max_iter=k).alpha
+        np.testing.assert_allclose(warm, a0 + cold, rtol=1e-9, atol=1e-9 * np.abs(a0).max())
+
+
+def test_warm_sigma0_closed_form_on_orthonormal_directions():
+    """With orthonormal directions, c I + U diag(D) U^T has eigenvalues c + D_k
+    along u_k and c on the complement; scaled to trace n."""
+    n, k = 10, 3
+    U, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((n, k)))
+    c, D = 0.7, np.array([2.0, 0.5, 5.0])
+    S = O.warm_sigma0(U, c, D)
+    s = n / (n * c + D.sum())
+    assert abs(np.trace(S) - n) < 1e-12 * n
+    np.testing.assert_allclose(S @ U, U * ((c + D) * s), rtol=1e-12, atol=1e-13)
+    v = np.linalg.qr(np.concatenate([U, np.random.default_rng(2).standard_normal((n, 1))], axis=1))[0][:, -1]
+    np.testing.assert_allclose(S @ v, c * s * v, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(O.warm_sigma0(U, 2.5, np.zeros(k)), np.eye(n), rtol=0, atol=1e-15)
+
+
+def test_warm_cccp_reaches_the_cold_fixed_point():
+    """The regularised MLE objective (Eq. prob:kernel-mle) is geodesically
+    convex in Sigma, as Tyler's M-estimator is, and the trace penalty makes
+    its minimiser unique, so CCCP reaches the same Sigma_* from any SPD start:
+    a warm start from a positive (c, D) must land on the cold start's answer,
+    and a start next to that answer must need fewer iterations."""
+    n, n_r = 24, 10
+    U, _ = _ubar(n, n_r, 2)
+    gamma, rho, eps = 0.1, 0.05, 1e-8
+    cold = O.cccp_fit(U, gamma, rho, eps, max_iter=500, tol=1e-12)
+    rng = np.random.default_rng(3)
+    warm = O.cccp_fit(U, gamma, rho, eps, max_iter=500, tol=1e-12,
+                      Sigma0=O.warm_sigma0(U, 0.3, rng.uniform(0.1, 3.0, n_r)))
+    assert cold.converged and warm.converged
+    np.testing.assert_allclose(warm.Sigma, cold.Sigma, rtol=0, atol=1e-9 * np.abs(cold.Sigma).max())
+    # started from a slightly perturbed copy of the answer: fewer iterations
+    near = O.cccp_fit(U, gamma, rho, eps, max_iter=500, tol=1e-12, Sigma0=cold.Sigma + 1e-4 * np.eye(n))
+    assert near.converged and near.iterations < cold.iterations
