@@ -179,6 +179,19 @@ def warm_sigma0(Ubar: np.ndarray, c: float, D: np.ndarray) -> np.ndarray:
     return S / (np.trace(S) / n)
 
 
+def low_rank_form(Sigma: np.ndarray, Ubar: np.ndarray) -> tuple:
+    """(c, D) with Sigma = c I + Ubar diag(D) Ubar^T, for a CCCP iterate over
+    N_r < n directions (every iterate from Sigma_0 = I has this form: F_gamma
+    adds multiples of u_k u_k^T and of I).  c is the eigenvalue of the
+    complement of span(Ubar), the smallest one; with M = Ubar^T Ubar,
+    diag(D) = M^-1 Ubar^T (Sigma - c I) Ubar M^-1 (least squares)."""
+    n = Sigma.shape[0]
+    c = float(np.linalg.eigvalsh(Sigma)[0])
+    M = Ubar.T @ Ubar
+    B = np.linalg.solve(M, np.linalg.solve(M, Ubar.T @ (Sigma - c * np.eye(n)) @ Ubar).T)
+    return c, np.diag(B).copy()
+
+
 def inverse_sqrt(Sigma: np.ndarray) -> np.ndarray:
     """P = Sigma^(-1/2)  (Eq. preconditioner-Sigmma), by a symmetric
     eigendecomposition Sigma = V diag(w) V^T, P = V diag(w^-1/2) V^T."""

@@ -656,3 +656,23 @@ def test_warm_cccp_reaches_the_cold_fixed_point():
     # started from a slightly perturbed copy of the answer: fewer iterations
     near = O.cccp_fit(U, gamma, rho, eps, max_iter=500, tol=1e-12, Sigma0=cold.Sigma + 1e-4 * np.eye(n))
     assert near.converged and near.iterations < cold.iterations
+
+
+def test_low_rank_form_round_trip():
+    """(c, D) read back from c I + U diag(D) U^T on non-orthogonal unit
+    directions, and from a CCCP iterate, which must have that form."""
+    n, n_r = 30, 6
+    U, _ = _ubar(n, n_r, 4)
+    c, D = 0.4, np.array([1.0, 0.2, 3.0, 0.05, 0.7, 2.2])
+    S = c * np.eye(n) + (U * D) @ U.T
+    c2, D2 = O.low_rank_form(S, U)
+    assert abs(c2 - c) < 1e-12
+    # the unit directions u_k = A z_k / |A z_k| are nearly collinear; D goes
+    # through M^-1 twice, so its error is ~kappa(M)^2 eps
+    kM = np.linalg.cond(U.T @ U)
+    np.testing.assert_allclose(D2, D, rtol=max(1e-12, 10 * kM ** 2 * 2.2e-16))
+    res = O.cccp_fit(U, 0.1, 0.05, 1e-8, max_iter=500, tol=1e-12)
+    c3, D3 = O.low_rank_form(res.Sigma, U)
+    np.testing.assert_allclose(c3 * np.eye(n) + (U * D3) @ U.T, res.Sigma, rtol=0,
+                               atol=10 * kM ** 2 * 2.2e-16 * np.abs(res.Sigma).max())
+    assert np.all(D3 > 0) and c3 > 0
