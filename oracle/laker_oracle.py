@@ -179,17 +179,22 @@ def warm_sigma0(Ubar: np.ndarray, c: float, D: np.ndarray) -> np.ndarray:
     return S / (np.trace(S) / n)
 
 
-def low_rank_form(Sigma: np.ndarray, Ubar: np.ndarray) -> tuple:
-    """(c, D) with Sigma = c I + Ubar diag(D) Ubar^T, for a CCCP iterate over
-    N_r < n directions (every iterate from Sigma_0 = I has this form: F_gamma
-    adds multiples of u_k u_k^T and of I).  c is the eigenvalue of the
-    complement of span(Ubar), the smallest one; with M = Ubar^T Ubar,
-    diag(D) = M^-1 Ubar^T (Sigma - c I) Ubar M^-1 (least squares)."""
-    n = Sigma.shape[0]
-    c = float(np.linalg.eigvalsh(Sigma)[0])
-    M = Ubar.T @ Ubar
-    B = np.linalg.solve(M, np.linalg.solve(M, Ubar.T @ (Sigma - c * np.eye(n)) @ Ubar).T)
-    return c, np.diag(B).copy()
+def cccp_step_coefficients(Sigma: np.ndarray, Ubar: np.ndarray, gamma: float, rho: float,
+                           eps: float) -> tuple:
+    """(c, D) of the next shrinkage-CCCP iterate written as c I + Ubar diag(D)
+    Ubar^T (Eqs. kernel_shrinkage_cccp_F, _Sigma, _normalization): F_gamma
+    puts the weight (n/N_r) / ((1 + gamma/n)(u_k^T Sigma^-1 u_k + eps)) on
+    u_k u_k^T and gamma / (1 + gamma/n) on I; the shrinkage scales the former
+    by 1 - rho and adds rho to the latter; the trace normalisation divides
+    both by tr / n, with tr = n a + sum_k w_k |u_k|^2.  At a converged Sigma_*
+    this is the low-rank form of Sigma_* itself (a fixed point)."""
+    n, n_r = Ubar.shape
+    c, low = scipy.linalg.cho_factor(Sigma, lower=True)
+    quad = np.sum(Ubar * scipy.linalg.cho_solve((c, low), Ubar), axis=0)
+    w = (1.0 - rho) * (n / n_r) / ((1.0 + gamma / n) * (quad + eps))
+    a = (1.0 - rho) * gamma / (1.0 + gamma / n) + rho
+    tr = n * a + float(np.sum(w * np.sum(Ubar * Ubar, axis=0)))
+    return a * n / tr, w * n / tr
 
 
 def inverse_sqrt(Sigma: np.ndarray) -> np.ndarray:

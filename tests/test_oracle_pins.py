@@ -658,21 +658,19 @@ def test_warm_cccp_reaches_the_cold_fixed_point():
     assert near.converged and near.iterations < cold.iterations
 
 
-def test_low_rank_form_round_trip():
-    """(c, D) read back from c I + U diag(D) U^T on non-orthogonal unit
-    directions, and from a CCCP iterate, which must have that form."""
+def test_cccp_step_coefficients_match_the_dense_update():
+    """The coefficient form of one CCCP step equals the dense step of
+    cccp_fit (cho_solve, explicit n x n sums) from an SPD start, and at the
+    converged Sigma_* it reproduces Sigma_* (fixed point)."""
     n, n_r = 30, 6
     U, _ = _ubar(n, n_r, 4)
-    c, D = 0.4, np.array([1.0, 0.2, 3.0, 0.05, 0.7, 2.2])
-    S = c * np.eye(n) + (U * D) @ U.T
-    c2, D2 = O.low_rank_form(S, U)
-    assert abs(c2 - c) < 1e-12
-    # the unit directions u_k = A z_k / |A z_k| are nearly collinear; D goes
-    # through M^-1 twice, so its error is ~kappa(M)^2 eps
-    kM = np.linalg.cond(U.T @ U)
-    np.testing.assert_allclose(D2, D, rtol=max(1e-12, 10 * kM ** 2 * 2.2e-16))
-    res = O.cccp_fit(U, 0.1, 0.05, 1e-8, max_iter=500, tol=1e-12)
-    c3, D3 = O.low_rank_form(res.Sigma, U)
-    np.testing.assert_allclose(c3 * np.eye(n) + (U * D3) @ U.T, res.Sigma, rtol=0,
-                               atol=10 * kM ** 2 * 2.2e-16 * np.abs(res.Sigma).max())
-    assert np.all(D3 > 0) and c3 > 0
+    gamma, rho, eps = 0.1, 0.05, 1e-8
+    S0 = O.warm_sigma0(U, 0.4, np.array([1.0, 0.2, 3.0, 0.05, 0.7, 2.2]))
+    c, D = O.cccp_step_coefficients(S0, U, gamma, rho, eps)
+    step = O.cccp_fit(U, gamma, rho, eps, max_iter=1, Sigma0=S0).Sigma
+    np.testing.assert_allclose(c * np.eye(n) + (U * D) @ U.T, step, rtol=0, atol=1e-12 * np.abs(step).max())
+    res = O.cccp_fit(U, gamma, rho, eps, max_iter=500, tol=1e-13)
+    c2, D2 = O.cccp_step_coefficients(res.Sigma, U, gamma, rho, eps)
+    np.testing.assert_allclose(c2 * np.eye(n) + (U * D2) @ U.T, res.Sigma, rtol=0,
+                               atol=1e-11 * np.abs(res.Sigma).max())
+    assert c2 > 0 and np.all(D2 > 0)
