@@ -130,6 +130,25 @@ laker_status laker_set_wait_budget(laker_ctx* ctx, int64_t cycles);
 laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int d,
                                 double scale, double lambda, int precision, int variant,
                                 laker_op** op);
+
+/*
+ * Streaming update (the paper's future work, Sec. VI: measurements that arrive
+ * one batch at a time; no counterpart in its experiments): a new operator over
+ * the n points of op followed by m new points.
+ *   Q_new   m x d embeddings of the new points (device, float64, row-major);
+ *           copied.
+ *   out     receives the new operator (n + m points, op's scale, lambda,
+ *           precision and resolved variant).  op stays valid and unchanged;
+ *           the caller destroys each.
+ * The stored entries of op are copied; only the tiles whose column block
+ * reaches a new point are evaluated (O(m (n + m) d) work plus a copy), by the
+ * same kernels as laker_build_kernel, so every product of the result equals
+ * that of laker_build_kernel on the concatenated embeddings bit for bit.
+ * Errors: LAKER_ERR_ARG for m < 1 or an operator of another device;
+ *         LAKER_ERR_NONFINITE for a non-finite Q_new entry; LAKER_ERR_OOM.
+ */
+laker_status laker_op_append(laker_ctx* ctx, const laker_op* op, const double* Q_new, int64_t m,
+                             laker_op** out);
 laker_status laker_op_destroy(laker_op* op);
 /* The operator's precision and the variant its products use; for an FP32
  * operator built with LAKER_AUTO also the measured time of one product of
@@ -206,6 +225,20 @@ laker_status laker_fit_preconditioner_seeded(laker_ctx* ctx, const laker_op* op,
                                              laker_precond** P, laker_fit_info* info);
 
 /*
+ * laker_fit_preconditioner started from a previous fit (streaming update; the
+ * warm start of Sec. IV-C's iteration, which the paper starts from
+ * Sigma_0 = I): Sigma_0 = c I + U diag(D) U^T with prev's (c, D) and this
+ * fit's normalised directions u_k, scaled to trace n.  The directions must
+ * continue prev's: Z is prev's Z with rows appended for the new points (the
+ * same n_r columns).  All other arguments, the result and the errors are those
+ * of laker_fit_preconditioner; LAKER_ERR_ARG also if prev is not a CCCP
+ * preconditioner over n_r directions.
+ */
+laker_status laker_fit_preconditioner_warm(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
+                                           double gamma, double rho, double eps, int max_iter, double tol,
+                                           const laker_precond* prev, laker_precond** P, laker_fit_info* info);
+
+/*
  * Gaussian random directions (Sec. IV-B, Eq. random_directions): Z (device,
  * n x n_r float64, row-major, column k = z_k) with entries N(0, 1) from the
  * counter-based generator Philox4x32-10 (Salmon et al., SC 2011) under the key
@@ -263,6 +296,20 @@ laker_status laker_precond_export(laker_ctx* ctx, const laker_precond* P, double
 laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
                              const double* y, double* alpha, double tol, int max_iter,
                              int refine_every, laker_solve_info* info);
+
+/*
+ * laker_pcg_solve from a caller-given start (streaming update: the previous
+ * solution with zeros for the new points).  alpha (device, n) holds the start
+ * alpha^0 on entry and the solution on return; r^0 = y - (lambda I + G)
+ * alpha^0 is formed with the float64-accurate product (one product, not
+ * counted in info->iterations), and the iteration is Algorithm 1's PCG from
+ * there.  A start that already meets tol returns with 0 iterations.
+ * Arguments, results and errors otherwise as laker_pcg_solve; also
+ * LAKER_ERR_NONFINITE for a non-finite start.
+ */
+laker_status laker_pcg_solve_warm(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
+                                  const double* y, double* alpha, double tol, int max_iter,
+                                  int refine_every, laker_solve_info* info);
 
 /*
  * laker_pcg_solve that also records, for every product k = 1 .. min(iterations,

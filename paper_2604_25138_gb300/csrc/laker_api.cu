@@ -212,6 +212,44 @@ laker_status laker_build_kernel(laker_ctx* ctx, const double* Q, int64_t n, int 
     return LAKER_OK;
 }
 
+laker_status laker_op_append(laker_ctx* ctx, const laker_op* op, const double* Q_new, int64_t m, laker_op** out) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !Q_new || !out) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (m < 1) return set_error(ctx, LAKER_ERR_ARG, "need m >= 1");
+    if (op->device != ctx->device) return set_error(ctx, LAKER_ERR_ARG, "operator belongs to another device");
+    if ((st = scan_finite(ctx, Q_new, m * op->d)) != LAKER_OK) return st;
+    laker_op* nop = new (std::nothrow) laker_op();
+    if (!nop) return LAKER_ERR_OOM;
+    nop->ctx = ctx;
+    nop->device = ctx->device;
+    nop->n = op->n + m;
+    nop->d = op->d;
+    nop->scale = op->scale;
+    nop->lambda = op->lambda;
+    nop->precision = op->precision;
+    nop->variant = op->variant;   // the variant the operator resolved to
+    const size_t qb = (size_t)op->n * op->d * sizeof(double);
+    if ((st = lk_malloc(ctx, (void**)&nop->Q64, qb + (size_t)m * op->d * sizeof(double))) != LAKER_OK) {
+        free_op(nop);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(nop->Q64, op->Q64, qb, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)nop->Q64 + qb, Q_new, (size_t)m * op->d * sizeof(double), cudaMemcpyDeviceToDevice,
+                            ctx->stream);
+    if (e != cudaSuccess) { free_op(nop); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    if ((st = build_operator(ctx, nop, op)) != LAKER_OK) { free_op(nop); return st; }
+    if (nop->precision == LAKER_FP32 && nop->variant == LAKER_MATRIX_FREE) {
+        if ((st = mf_prepare(ctx, nop)) != LAKER_OK) { free_op(nop); return st; }
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { free_op(nop); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }
+    *out = nop;
+    return LAKER_OK;
+}
+
 laker_status laker_op_describe(const laker_op* op, int* precision, int* variant, double* t_materialised_ms,
                                double* t_matrix_free_ms) {
     if (!op) return LAKER_ERR_ARG;
@@ -277,6 +315,30 @@ laker_status laker_fit_preconditioner(laker_ctx* ctx, const laker_op* op, const 
     P->device = ctx->device;
     P->use32 = op->precision != LAKER_FP64;
     st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info);
+    if (st != LAKER_OK) { free_precond(P); return st; }
+    *out = P;
+    return LAKER_OK;
+}
+
+laker_status laker_fit_preconditioner_warm(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
+                                           double gamma, double rho, double eps, int max_iter, double tol,
+                                           const laker_precond* prev, laker_precond** out, laker_fit_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !Z || !out || !prev) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (n_r < 1 || n_r > LK_MAX_NR) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 2048");
+    if (prev->kind != PRECOND_CCCP || prev->n_r != n_r || !prev->D)
+        return set_error(ctx, LAKER_ERR_ARG, "warm start needs a CCCP preconditioner over the same n_r directions");
+    if (!(gamma >= 0.0) || !(eps > 0.0) || rho > 1.0 || max_iter < 1 || !(tol >= 0.0))
+        return set_error(ctx, LAKER_ERR_ARG, "bad CCCP parameters");
+    if ((st = scan_finite(ctx, Z, op->n * (int64_t)n_r)) != LAKER_OK) return st;
+    laker_precond* P = new (std::nothrow) laker_precond();
+    if (!P) return LAKER_ERR_OOM;
+    P->ctx = ctx;
+    P->device = ctx->device;
+    P->use32 = op->precision != LAKER_FP64;
+    st = fit_cccp(ctx, op, Z, n_r, gamma, rho, eps, max_iter, tol, P, info, nullptr, nullptr, 0, prev);
     if (st != LAKER_OK) { free_precond(P); return st; }
     *out = P;
     return LAKER_OK;
@@ -399,6 +461,18 @@ laker_status laker_pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_pre
     if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
     if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
     return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info);
+}
+
+laker_status laker_pcg_solve_warm(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
+                                  double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info) {
+    laker_status st = check_ctx(ctx);
+    if (st != LAKER_OK) return st;
+    if (!op || !y || !alpha) return set_error(ctx, LAKER_ERR_ARG, "null pointer");
+    if (!(tol >= 0.0) || max_iter < 1 || refine_every < 0) return set_error(ctx, LAKER_ERR_ARG, "bad PCG parameters");
+    if (P && P->n != op->n) return set_error(ctx, LAKER_ERR_ARG, "preconditioner size mismatch");
+    if ((st = scan_finite(ctx, y, op->n)) != LAKER_OK) return st;
+    if ((st = scan_finite(ctx, alpha, op->n)) != LAKER_OK) return st;
+    return pcg_solve(ctx, op, P, y, alpha, tol, max_iter, refine_every, info, nullptr, 0, 0.0, 0.0, true);
 }
 
 laker_status laker_pcg_solve_trace(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,

@@ -31,13 +31,11 @@ __device__ __forceinline__ int64_t pk_tile(int I, int J, int nb) {
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_build_sym(const double* __restrict__ Q, int64_t n, int d, double scale,
-            double* __restrict__ K64, float* __restrict__ K32, float* __restrict__ K32lo, int64_t ldk, int nt) {
+            double* __restrict__ K64, float* __restrict__ K32, float* __restrict__ K32lo, int64_t ldk, int nt, int j0) {
     constexpr bool PAIR = MODE != 0;
-    // blockIdx.x enumerates the upper-triangular tile pairs row by row.
-    int64_t t = blockIdx.x;
-    int bi = 0;
-    while (t >= nt - bi) { t -= nt - bi; ++bi; }
-    const int bj = bi + (int)t;
+    // blockIdx.x enumerates the upper-triangular tile pairs with bj >= j0
+    int bi, bj;
+    lk::upper_pair(blockIdx.x, nt, j0, bi, bj);
 
     __shared__ double sm[2 * BD * (BT + 1)];
     double (*Qi)[BT + 1] = reinterpret_cast<double (*)[BT + 1]>(sm);
@@ -157,11 +155,30 @@ __global__ void k_split_bf16(const double* __restrict__ Q, int64_t n, int d, int
 
 }  // namespace
 
-laker_status build_operator(laker_ctx* ctx, laker_op* op) {
+// Copy the 128 x 128 packed tiles (I, J), I <= J < J0, of an operator over
+// fewer blocks into the packed layout of nb blocks: row I's run of tiles is
+// contiguous in both layouts.
+laker_status copy_packed_tiles(laker_ctx* ctx, const float* src, int nb_src, float* dst, int nb, int J0) {
+    const size_t tile = (size_t)2 * 128 * 128 * sizeof(float);
+    for (int I = 0; I < J0; ++I) {
+        const int64_t a = (int64_t)I * nb_src - (int64_t)I * (I - 1) / 2;
+        const int64_t b = (int64_t)I * nb - (int64_t)I * (I - 1) / 2;
+        LK_CUDA(ctx, cudaMemcpyAsync((char*)dst + b * tile, (const char*)src + a * tile, (size_t)(J0 - I) * tile,
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return LAKER_OK;
+}
+
+laker_status build_operator(laker_ctx* ctx, laker_op* op, const laker_op* prev) {
     const int64_t n = op->n;
     const int d = op->d;
     op->ldk = (n + 3) / 4 * 4;
     op->dpad = (d + 15) / 16 * 16;
+    // prev: the same operator over the first prev->n points; its stored
+    // entries are copied and only the tile pairs whose column block reaches
+    // the new points are evaluated (the same kernels on the same tiles, so the
+    // result equals a fresh build bit for bit)
+    const int64_t n0 = prev ? prev->n : 0;
     // FP64: float64 G; FP32: the float32 pair, full (its float32 product
     // streams rows of hi); BF16X3: the pair packed in the upper triangle, read
     // only by the float64-accurate product (the operator is matrix-free)
@@ -188,23 +205,42 @@ laker_status build_operator(laker_ctx* ctx, laker_op* op) {
                                            ctx->stream));
         }
     }
+    if (prev && mode != 2) {
+        if (mode == 1) {
+            LK_CUDA(ctx, cudaMemcpy2DAsync(op->K32, op->ldk * sizeof(float), prev->K32, prev->ldk * sizeof(float),
+                                           n0 * sizeof(float), n0, cudaMemcpyDeviceToDevice, ctx->stream));
+            LK_CUDA(ctx, cudaMemcpy2DAsync(op->K32lo, op->ldk * sizeof(float), prev->K32lo, prev->ldk * sizeof(float),
+                                           n0 * sizeof(float), n0, cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            LK_CUDA(ctx, cudaMemcpy2DAsync(op->K64, op->ldk * sizeof(double), prev->K64, prev->ldk * sizeof(double),
+                                           n0 * sizeof(double), n0, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    }
     if (mode == 2 && d <= 64) {
-        if ((st = resid_build_df(ctx, op)) != LAKER_OK) return st;
+        if ((st = resid_build_df(ctx, op, prev)) != LAKER_OK) return st;
     } else if (mode == 2) {
         const int nb128 = (int)((n + 127) / 128);
         const int nt = 2 * nb128;   // 64-blocks, padded so that every packed tile is written
-        const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
-        k_build_sym<2><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, Kp, nullptr,
-                                                                 nb128, nt);
+        const int J0 = prev ? (int)(n0 / 128) : 0;   // whole 128-blocks of the previous operator
+        if (prev && (st = copy_packed_tiles(ctx, resid_packed(prev), (int)((n0 + 127) / 128), Kp, nb128, J0)) !=
+                        LAKER_OK)
+            return st;
+        const int64_t pairs = lk::upper_pairs(nt, 2 * J0);
+        if (pairs > 0)
+            k_build_sym<2><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, Kp, nullptr,
+                                                                     nb128, nt, 2 * J0);
     } else {
         const int nt = (int)((n + BT - 1) / BT);
-        const int64_t pairs = (int64_t)nt * (nt + 1) / 2;
-        if (mode == 1)
-            k_build_sym<1><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, op->K32,
-                                                                     op->K32lo, op->ldk, nt);
-        else
-            k_build_sym<0><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64, nullptr,
-                                                                     nullptr, op->ldk, nt);
+        const int j0 = prev ? (int)(n0 / BT) : 0;   // whole tiles of the previous operator
+        const int64_t pairs = lk::upper_pairs(nt, j0);
+        if (pairs > 0) {
+            if (mode == 1)
+                k_build_sym<1><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, nullptr, op->K32,
+                                                                         op->K32lo, op->ldk, nt, j0);
+            else
+                k_build_sym<0><<<(unsigned)pairs, 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->K64, nullptr,
+                                                                         nullptr, op->ldk, nt, j0);
+        }
     }
     if (!(mode == 2 && d <= 64)) LK_LAUNCHED(ctx);
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(op->Q64, n, d, op->scale, op->lambda,

@@ -103,4 +103,26 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int* err, long long budg
     return ok_s != 0;
 }
 
+// Block pairs (I, J) of an upper triangle, I <= J < nb, restricted to J >= j0
+// (j0 = 0: all of them).  An operator extended by new points recomputes only
+// the pairs whose column block reaches them.  Order: the rectangle I < j0 row
+// by row, then the triangle j0 <= I <= J row by row.
+__host__ __device__ __forceinline__ int64_t upper_pairs(int nb, int j0) {
+    const int64_t w = nb - j0;
+    return (int64_t)j0 * w + w * (w + 1) / 2;
+}
+__host__ __device__ __forceinline__ void upper_pair(int64_t t, int nb, int j0, int& I, int& J) {
+    const int64_t w = nb - j0;
+    if (t < (int64_t)j0 * w) {
+        I = (int)(t / w);
+        J = j0 + (int)(t % w);
+        return;
+    }
+    t -= (int64_t)j0 * w;
+    int i = j0;
+    while (t >= nb - i) { t -= nb - i; ++i; }
+    I = i;
+    J = i + (int)t;
+}
+
 }  // namespace lk

@@ -706,7 +706,7 @@ unsigned gsz(int64_t count, int b = 256) { return (unsigned)((count + b - 1) / b
 
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r, double gamma, double rho,
                       double eps, int max_iter, double tol, laker_precond* P, laker_fit_info* info, laker_setnet* net,
-                      const float* Xpts, int mode) {
+                      const float* Xpts, int mode, const laker_precond* warm) {
     const int64_t n = op->n;
     const int nr = n_r;
     const int NP = (nr + NB - 1) / NB * NB;
@@ -772,25 +772,33 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     CccpState h{};
     h.c = 1.0;
     LK_CUDA(ctx, cudaMemsetAsync(D, 0, NP * sizeof(double), s));
-    if (net) {
-        // Sigma_0 = c0 I + U diag(D0) U^T from the set network, scaled to tr = n
-        const float *logc = nullptr, *logD = nullptr;
-        if ((st = setnet_predict(ctx, net, n, Xpts, nr, P->feat, &logc, &logD)) != LAKER_OK) return st;
-        std::vector<float> hD((size_t)nr);
-        float hc = 0.f;
-        LK_CUDA(ctx, cudaMemcpyAsync(&hc, logc, sizeof(float), cudaMemcpyDeviceToHost, s));
-        LK_CUDA(ctx, cudaMemcpyAsync(hD.data(), logD, sizeof(float) * nr, cudaMemcpyDeviceToHost, s));
-        LK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (net || warm) {
+        // Sigma_0 = c0 I + U diag(D0) U^T, scaled to tr = n (M_kk = 1): from the
+        // set network's prediction, or from a previous fit's (c, D) over the
+        // same directions extended to the new points (streaming update)
         std::vector<double> D0((size_t)nr);
-        double tr = (double)n * std::exp((double)hc);
-        for (int k = 0; k < nr; ++k) {
-            D0[(size_t)k] = std::exp(std::min(50.0, (double)hD[(size_t)k]));   // M_kk = 1
-            tr += D0[(size_t)k];
+        double c0 = 0.0;
+        if (net) {
+            const float *logc = nullptr, *logD = nullptr;
+            if ((st = setnet_predict(ctx, net, n, Xpts, nr, P->feat, &logc, &logD)) != LAKER_OK) return st;
+            std::vector<float> hD((size_t)nr);
+            float hc = 0.f;
+            LK_CUDA(ctx, cudaMemcpyAsync(&hc, logc, sizeof(float), cudaMemcpyDeviceToHost, s));
+            LK_CUDA(ctx, cudaMemcpyAsync(hD.data(), logD, sizeof(float) * nr, cudaMemcpyDeviceToHost, s));
+            LK_CUDA(ctx, cudaStreamSynchronize(s));
+            c0 = std::exp((double)hc);
+            for (int k = 0; k < nr; ++k) D0[(size_t)k] = std::exp(std::min(50.0, (double)hD[(size_t)k]));
+        } else {
+            LK_CUDA(ctx, cudaMemcpyAsync(D0.data(), warm->D, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+            LK_CUDA(ctx, cudaStreamSynchronize(s));
+            c0 = warm->c;
         }
+        double tr = (double)n * c0;
+        for (int k = 0; k < nr; ++k) tr += D0[(size_t)k];
         const double f = (double)n / tr;
-        h.c = std::exp((double)hc) * f;
+        h.c = c0 * f;
         for (double& v : D0) v *= f;
-        if (!(h.c > 0.0) || !std::isfinite(h.c)) return set_error(ctx, LAKER_ERR_NONFINITE, "learned start: bad c");
+        if (!(h.c > 0.0) || !std::isfinite(h.c)) return set_error(ctx, LAKER_ERR_NONFINITE, "warm start: bad c");
         LK_CUDA(ctx, cudaMemcpyAsync(D, D0.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, s));
     }
     LK_CUDA(ctx, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s));

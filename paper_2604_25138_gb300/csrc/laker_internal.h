@@ -128,20 +128,24 @@ laker_status lk_malloc(laker_ctx* ctx, void** p, size_t bytes);
 
 // ---- translation-unit entry points ---------------------------------------
 // laker_build.cu
-laker_status build_operator(laker_ctx* ctx, laker_op* op);
+// prev (may be null): the same operator over the first prev->n points, whose
+// stored entries are reused (streaming append)
+laker_status build_operator(laker_ctx* ctx, laker_op* op, const laker_op* prev = nullptr);
+laker_status copy_packed_tiles(laker_ctx* ctx, const float* src, int nb_src, float* dst, int nb, int J0);
 laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
 laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
 // laker_pcg.cu
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
                        const double* y, double* alpha, double tol, int max_iter,
                        int refine_every, laker_solve_info* info, double* trace = nullptr,
-                       int trace_cap = 0, double R_ref = 0.0, double gap_tol = 0.0);
+                       int trace_cap = 0, double R_ref = 0.0, double gap_tol = 0.0, bool warm = false);
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
 // laker_fit.cu
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
                       double gamma, double rho, double eps, int max_iter, double tol,
                       laker_precond* P, laker_fit_info* info,
-                      laker_setnet* net = nullptr, const float* X = nullptr, int mode = 0);
+                      laker_setnet* net = nullptr, const float* X = nullptr, int mode = 0,
+                      const laker_precond* warm = nullptr);
 // laker_map.cu
 laker_status eval_map(laker_ctx* ctx, const laker_op* op, const double* Qg, int64_t m,
                       const double* alpha, double* out, int method);
@@ -161,7 +165,8 @@ laker_status dirs_tc(laker_ctx* ctx, const laker_op* op, const double* Z, int nr
 // laker_resid.cu (float64-accurate product from the packed upper-triangular pair)
 laker_status resid_prepare(laker_ctx* ctx, laker_op* op, float** Kp);
 void resid_release(laker_op* op);
-laker_status resid_build_df(laker_ctx* ctx, const laker_op* op);
+laker_status resid_build_df(laker_ctx* ctx, const laker_op* op, const laker_op* prev = nullptr);
+const float* resid_packed(const laker_op* op);   // the packed pair of a split-bf16 operator
 laker_status resid_status(laker_ctx* ctx, const laker_op* op);
 laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, double* w, const PcgScalars* sc,
                           int gate);

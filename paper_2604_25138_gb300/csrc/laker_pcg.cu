@@ -293,6 +293,54 @@ k_pcg_init(int64_t n, const double* __restrict__ y, double* __restrict__ alpha, 
     }
 }
 
+// Warm start: alpha holds the caller's start alpha^0 and w2 = (lambda I + G)
+// alpha^0 (float64-accurate); r^0 = y - w2.  A start that already meets the
+// tolerance ends the solve before the first product.
+__global__ void __launch_bounds__(VEC_THREADS)
+k_pcg_init_warm(int64_t n, const double* __restrict__ y, const double* __restrict__ alpha,
+                const double* __restrict__ w2, double* __restrict__ r, double* __restrict__ p0,
+                double* __restrict__ abest, double* __restrict__ rbest, PcgScalars* sc,
+                double* __restrict__ partials, double tol) {
+    __shared__ double red[VEC_THREADS / 32];
+    int64_t r0, r1;
+    row_range(n, r0, r1);
+    double yy = 0.0, rr = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double yi = y[i];
+        const double ri = yi - w2[i];
+        r[i] = ri;
+        p0[i] = 0.0;
+        abest[i] = alpha[i];   // the guard's fallback before its first replacement
+        rbest[i] = ri;
+        yy = fma(yi, yi, yy);
+        rr = fma(ri, ri, rr);
+    }
+    yy = lk::block_sum(yy, red);
+    rr = lk::block_sum(rr, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = yy;
+        partials[gridDim.x + blockIdx.x] = rr;
+    }
+    if (lk::last_block(&sc->ticket[1])) {
+        const double tyy = lk::sum_partials(partials, gridDim.x, red);
+        const double trr = lk::sum_partials(partials + gridDim.x, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            sc->yy = tyy;
+            sc->rr = trr;
+            sc->rr_true = trr;
+            sc->tol2yy = tol * tol * tyy;
+            sc->rz = 0.0;
+            sc->beta = 0.0;
+            sc->delta = 0.0;
+            sc->iters = 0;
+            sc->true_count = 0;
+            sc->need_true = 0;
+            sc->converged = (!isfinite(tyy) || !isfinite(trr)) ? 2 : (trr <= sc->tol2yy ? 1 : 0);
+            sc->ticket[1] = 0;
+        }
+    }
+}
+
 // UPD: alpha += delta p, r -= delta w, |r|^2; stop / refinement decisions.
 __global__ void __launch_bounds__(VEC_THREADS)
 k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ alpha,
@@ -993,7 +1041,7 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
 
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
                        double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info,
-                       double* trace, int trace_cap, double R_ref, double gap_tol) {
+                       double* trace, int trace_cap, double R_ref, double gap_tol, bool warm) {
     const int64_t n = op->n;
     const bool mixed = (op->precision != LAKER_FP64) && refine_every > 0;
     const bool use32 = (op->precision != LAKER_FP64);
@@ -1030,10 +1078,17 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     LK_CUDA(ctx, cudaMemcpyAsync(ws.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
 
     auto run_init = [&]() -> laker_status {
-        k_pcg_init<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, alpha, ws.r, ws.p[0], ws.abest, ws.rbest,
-                                                                   ws.sc, ws.partials, tol);
-        LK_LAUNCHED(ctx);
         laker_status s2;
+        if (warm) {
+            if ((s2 = op_matvec_fp64(ctx, op, alpha, ws.w2)) != LAKER_OK) return s2;
+            k_pcg_init_warm<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, alpha, ws.w2, ws.r, ws.p[0],
+                                                                            ws.abest, ws.rbest, ws.sc, ws.partials,
+                                                                            tol);
+        } else {
+            k_pcg_init<<<ws.vec_blocks, VEC_THREADS, 0, ctx->stream>>>(n, y, alpha, ws.r, ws.p[0], ws.abest,
+                                                                       ws.rbest, ws.sc, ws.partials, tol);
+        }
+        LK_LAUNCHED(ctx);
         if (use32) {
             if ((s2 = launch_utr<float>(ctx, n, pv, ws.r, (float*)ws.t, ws.sc, GATE_RUNNING)) != LAKER_OK) return s2;
             k_precond<float><<<ws.pre_blocks, VEC_THREADS, 0, ctx->stream>>>(n, ws.r, ws.z, ws.sc, ws.partials, pv,

@@ -267,14 +267,13 @@ __global__ void k_df_sym_finish(RSched sch, int64_t n, double lambda, const doub
 // to ~2^-46.  Stores are coalesced along j.  Entries with i or j >= n are 0.
 template <int DM>
 __global__ void __launch_bounds__(256)
-k_build_packed_df(const float2* __restrict__ Qs, int64_t n, int d, int nb, float* __restrict__ Kp) {
+k_build_packed_df(const float2* __restrict__ Qs, int64_t n, int d, int nb, int j0, float* __restrict__ Kp) {
     extern __shared__ float2 qi_s[];             // 128 rows x DM df values of block I
     __shared__ float e2tab[128];
     lk::df_exp_table_init(e2tab);
-    const int64_t t = blockIdx.x;
-    int I = 0;
-    while (I + 1 < nb && r_row_start(I + 1, nb) <= t) ++I;
-    const int J = I + (int)(t - r_row_start(I, nb));
+    int I, J;                                    // tiles with J >= j0 (all: j0 = 0)
+    lk::upper_pair(blockIdx.x, nb, j0, I, J);
+    const int64_t t = r_row_start(I, nb) + (J - I);
     for (int idx = threadIdx.x; idx < RT * DM; idx += blockDim.x) {
         const int r = idx / DM, k = idx % DM;
         const int64_t i = (int64_t)I * RT + r;
@@ -393,12 +392,28 @@ laker_status resid_matvec(laker_ctx* ctx, const laker_op* op, const double* x, d
     return LAKER_OK;
 }
 
+const float* resid_packed(const laker_op* op) {
+    const ResidWork* rw = static_cast<const ResidWork*>(op->rw);
+    return rw ? rw->Kp : nullptr;
+}
+
 // Fill the packed pair of a split-bf16 operator (d <= 64) in double-float.
-laker_status resid_build_df(laker_ctx* ctx, const laker_op* op) {
+// prev: the same operator over the first prev->n points; its tiles (I, J)
+// with J below the first block that reaches a new point are copied, the rest
+// are evaluated.
+laker_status resid_build_df(laker_ctx* ctx, const laker_op* op, const laker_op* prev) {
     const ResidWork* rw = static_cast<const ResidWork*>(op->rw);
     if (!rw) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "packed pair not allocated");
     const int64_t n = op->n;
     const int d = op->d;
+    const int J0 = prev ? (int)(prev->n / RT) : 0;
+    if (prev) {
+        const ResidWork* pw = static_cast<const ResidWork*>(prev->rw);
+        if (!pw) return set_error(ctx, LAKER_ERR_UNSUPPORTED, "previous operator has no packed pair");
+        laker_status s2 = copy_packed_tiles(ctx, pw->Kp, pw->sch.nb, rw->Kp, rw->sch.nb, J0);
+        if (s2 != LAKER_OK) return s2;
+    }
+    const int64_t tiles = lk::upper_pairs(rw->sch.nb, J0);
     float2* Qs = nullptr;
     laker_status st = lk_malloc(ctx, (void**)&Qs, (size_t)n * d * sizeof(float2));
     if (st != LAKER_OK) return st;
@@ -409,8 +424,8 @@ laker_status resid_build_df(laker_ctx* ctx, const laker_op* op) {
     cudaError_t e = cudaSuccess;
 #define LK_PB(D)                                                                                                  \
     e = cudaFuncSetAttribute(k_build_packed_df<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-    if (e == cudaSuccess)                                                                                         \
-        k_build_packed_df<D><<<(unsigned)rw->sch.T, 256, smem, ctx->stream>>>(Qs, n, d, rw->sch.nb, rw->Kp)
+    if (e == cudaSuccess && tiles > 0)                                                                            \
+        k_build_packed_df<D><<<(unsigned)tiles, 256, smem, ctx->stream>>>(Qs, n, d, rw->sch.nb, J0, rw->Kp)
     if (dm == 16) { LK_PB(16); } else if (dm == 32) { LK_PB(32); } else { LK_PB(64); }
 #undef LK_PB
     if (e != cudaSuccess) { cudaFree(Qs); return set_error(ctx, LAKER_ERR_CUDA, cudaGetErrorString(e)); }

@@ -115,6 +115,10 @@ def library() -> ctypes.CDLL:
         "laker_prediction_discrepancy": (i32, [vp, vp, vp, vp, ctypes.POINTER(f64)]),
         "laker_setnet_save": (i32, [vp, vp, ctypes.c_char_p]),
         "laker_setnet_load": (i32, [vp, ctypes.c_char_p, pvp]),
+        "laker_op_append": (i32, [vp, vp, vp, i64, pvp]),
+        "laker_pcg_solve_warm": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
+        "laker_fit_preconditioner_warm": (i32, [vp, vp, vp, i32, f64, f64, f64, i32, f64, vp, pvp,
+                                                ctypes.POINTER(FitInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -230,6 +234,18 @@ def laker_build_kernel(ctx: Context, Q: torch.Tensor, scale: float, lam: float, 
         ctx.check(library().laker_build_kernel(ctx.handle, _ptr(Q, "Q"), n, d, scale, lam, precision, variant,
                                                ctypes.byref(h)))
     return Operator(ctx, h, n, d, precision, variant, Q)
+
+
+def laker_op_append(ctx: Context, op: Operator, Q_new: torch.Tensor) -> Operator:
+    """Streaming update: the operator over op's points followed by the rows of
+    Q_new (m x d), reusing op's stored entries.  op stays valid."""
+    m, d = Q_new.shape
+    if d != op.d:
+        raise ValueError("Q_new has %d columns, the operator %d" % (d, op.d))
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_op_append(ctx.handle, op.handle, _ptr(Q_new, "Q_new", m * d), m, ctypes.byref(h)))
+    return Operator(ctx, h, op.n + m, d, op.precision, op.variant, torch.cat([op.Q, Q_new]))
 
 
 def laker_op_describe(op: Operator) -> dict:
@@ -571,6 +587,36 @@ def laker_fit_preconditioner_seeded(ctx: Context, op: Operator, seed: int, n_r: 
                                                             max_iter, tol, ctypes.byref(h), ctypes.byref(info)))
     d = {f: getattr(info, f) for f, _ in FitInfo._fields_}
     return Preconditioner(ctx, h, op.n, n_r, d)
+
+
+def laker_fit_preconditioner_warm(ctx: Context, op: Operator, Z: torch.Tensor, prev: Preconditioner,
+                                  gamma: float = 0.1, rho: float = -1.0, eps: float = 1e-8, max_iter: int = 200,
+                                  tol: float = 1e-10) -> Preconditioner:
+    """CCCP fit started from a previous fit's (c, D); Z continues prev's
+    directions with rows for the new points."""
+    n, n_r = Z.shape
+    info = FitInfo()
+    h = ctypes.c_void_p()
+    with ctx:
+        ctx.check(library().laker_fit_preconditioner_warm(ctx.handle, op.handle, _ptr(Z, "Z", op.n * n_r), n_r,
+                                                          gamma, rho, eps, max_iter, tol, prev.handle,
+                                                          ctypes.byref(h), ctypes.byref(info)))
+    d = {f: getattr(info, f) for f, _ in FitInfo._fields_}
+    return Preconditioner(ctx, h, op.n, n_r, d)
+
+
+def laker_pcg_solve_warm(ctx: Context, op: Operator, P: Preconditioner | None, y: torch.Tensor,
+                         alpha0: torch.Tensor, tol: float, max_iter: int = 100000, refine_every: int = 0,
+                         allow_maxiter: bool = False):
+    """PCG from the start alpha0 (not modified); returns (alpha, info)."""
+    alpha = alpha0.clone()
+    info = SolveInfo()
+    with ctx:
+        st = library().laker_pcg_solve_warm(ctx.handle, op.handle, P.handle if P is not None else None,
+                                            _ptr(y, "y", op.n), _ptr(alpha, "alpha", op.n), tol, max_iter,
+                                            refine_every, ctypes.byref(info))
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    return alpha, {f: getattr(info, f) for f, _ in SolveInfo._fields_}
 
 
 def laker_random_directions(ctx: Context, seed: int, n: int, n_r: int) -> torch.Tensor:
