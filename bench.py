@@ -844,6 +844,121 @@ def run_combined(args):
     print(json.dumps(line))
 
 
+def run_streaming(args):
+    """Streaming update (the paper's future work: measurements that arrive
+    sequentially).  The 16384-point clustered instance (d = 32, lambda = 1e-4,
+    8 Tx) is solved once; then `--stream-steps` batches of `--stream-m` new
+    points of the same field arrive.  A timed update is: laker_op_append
+    (reusing the stored entries), the CCCP fit warm-started from the previous
+    (c, D), and PCG warm-started from the previous alpha (zeros for the new
+    points), mixed split-bf16, to a true relative residual of 1e-6.  The
+    baseline redoes each update cold: build, fit from Sigma_0 = I, PCG from
+    0.  N_r stays at the first instance's value so that the warm fit keeps its
+    directions (Z grows by rows)."""
+    import torch
+
+    from paper_2604_25138_gb300 import build
+    from paper_2604_25138_gb300 import laker as L
+
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = L.Context(0)
+    n0, m, steps = 16384, args.stream_m, args.stream_steps
+    n = n0 + m * steps
+    inst = synth.make_instance(n, 32, 1e-4, n_tx=8, seed=2000, layout="clustered", grid=2)
+    n_r = synth.default_num_directions(n0)
+    tol = 1e-6
+
+    def dev(x):
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+    Q, y, Z = dev(inst.Q), dev(inst.y), dev(synth.directions(n, n_r, 2000))
+
+    def first():
+        op = L.laker_build_kernel(ctx, Q[:n0].contiguous(), inst.scale, inst.lam, L.BF16X3)
+        P = L.laker_fit_preconditioner(ctx, op, Z[:n0].contiguous())
+        a, f = L.laker_pcg_solve(ctx, op, P, y[:n0].contiguous(), tol, max_iter=40000, refine_every=20)
+        return op, P, a
+
+    def warm_run():
+        op, P, a = first()
+        rows = []
+        for s_ in range(steps):
+            k = n0 + (s_ + 1) * m
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op1 = L.laker_op_append(ctx, op, Q[k - m:k].contiguous())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            P1 = L.laker_fit_preconditioner_warm(ctx, op1, Z[:k].contiguous(), P)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            a0 = torch.cat([a, torch.zeros(m, dtype=torch.float64, device="cuda")])
+            a, f = L.laker_pcg_solve_warm(ctx, op1, P1, y[:k].contiguous(), a0, tol, max_iter=40000,
+                                          refine_every=20)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            rows.append(dict(n=k, append_ms=1e3 * (t1 - t0), fit_ms=1e3 * (t2 - t1), solve_ms=1e3 * (t3 - t2),
+                             products=f["iterations"], cccp_iterations=P1.info["iterations"],
+                             rel_res_true=f["rel_res_true"], restarts=f["restarts"]))
+            P.close()
+            op.close()
+            op, P = op1, P1
+        P.close()
+        op.close()
+        return rows
+
+    def cold_run():
+        rows = []
+        for s_ in range(steps):
+            k = n0 + (s_ + 1) * m
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op = L.laker_build_kernel(ctx, Q[:k].contiguous(), inst.scale, inst.lam, L.BF16X3)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            P = L.laker_fit_preconditioner(ctx, op, Z[:k].contiguous())
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            a, f = L.laker_pcg_solve(ctx, op, P, y[:k].contiguous(), tol, max_iter=40000, refine_every=20)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            rows.append(dict(n=k, build_ms=1e3 * (t1 - t0), fit_ms=1e3 * (t2 - t1), solve_ms=1e3 * (t3 - t2),
+                             products=f["iterations"], cccp_iterations=P.info["iterations"],
+                             rel_res_true=f["rel_res_true"]))
+            P.close()
+            op.close()
+        return rows
+
+    warm_run()   # warm-up (also compiles nothing: the library is built)
+    launches0 = ctx.launches()
+    with ClockSampler(0) as clk:
+        warm = warm_run()
+    launches = ctx.launches() - launches0
+    cold = cold_run()
+
+    def tot(rows, keys):
+        return sum(sum(r[k] for k in keys) for r in rows)
+
+    warm_ms = tot(warm, ("append_ms", "fit_ms", "solve_ms"))
+    cold_ms = tot(cold, ("build_ms", "fit_ms", "solve_ms"))
+    line = {
+        "metric": "streaming updates/s at true rel-res 1e-6 (append + warm CCCP + warm PCG, mixed)",
+        "value": steps / (warm_ms / 1e3), "unit": "updates/s", "n_gpus": 1, "steps": steps, "warmup": 1,
+        "ms_per_step": warm_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3 operator, f64 residual and scalars", "data": "synthetic",
+        "config": {"workload": "streaming: n0 = 16384 clustered (d = 32, lambda = 1e-4, 8 Tx), %d batches of %d "
+                               "new points, N_r = %d" % (steps, m, n_r)},
+        "cold_updates_per_s": steps / (cold_ms / 1e3),
+        "speedup_vs_cold": cold_ms / warm_ms,
+        "warm": warm, "cold": cold,
+        "worst_rel_res_true": max(r["rel_res_true"] for r in warm),
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 # ---------------------------------------------------------------------------
 # The FP64 oracle on the host cores (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
@@ -938,7 +1053,7 @@ def main():
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[50, 200, 500, 1000, 2000, 4000, 8000])
     ap.add_argument("--gd-steps", type=int, default=2000)
     ap.add_argument("--variant-sizes", type=int, nargs="+", default=[512, 1024, 2048, 4096, 8192, 16384, 32768])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "batched", "learned", "sweep", "variants", "combined"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "batched", "learned", "sweep", "variants", "combined", "streaming"],
                     help="c3: the precision-form instance n=65536, d=64 (the headline line); c2: the n=16384 "
                          "instance; batched: 256 instances; learned: the set-network preconditioner")
     ap.add_argument("--learned-train", type=int, default=256)
@@ -947,6 +1062,8 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=2000)
     ap.add_argument("--combined-count", type=int, default=96)
     ap.add_argument("--combined-cap", type=int, default=4000)
+    ap.add_argument("--stream-m", type=int, default=512)
+    ap.add_argument("--stream-steps", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -960,6 +1077,8 @@ def main():
         run_variants(args)
     elif args.workload == "combined":
         run_combined(args)
+    elif args.workload == "streaming":
+        run_streaming(args)
     else:
         run_ours(args)
 

@@ -151,10 +151,12 @@ def random_vector(n: int, seed: int) -> np.ndarray:
 def default_num_directions(n: int) -> int:
     """The number of random directions N_r.  The paper gives only the shape of
     its schedule (O(sqrt n) for small n, linear for large n, Sec. V-A); this
-    reading takes max(4 sqrt(n), n/16), at most n and 1024: 128 at n = 1024,
-    1024 at n = 16384 and at n = 65536 (the fit's cost grows like
-    n N_r^2 + N_r^3 while the PCG products fall slowly with N_r)."""
-    return int(min(n, 1024, max(math.ceil(4.0 * math.sqrt(n)), math.ceil(n / 16.0))))
+    reading takes max(2 sqrt(n), n/64), at most n and 1024: 64 at n = 1024,
+    128 at n = 4096, 256 at n = 16384, 1024 at n = 65536.  The constants are
+    measured: the fit's cost grows like n N_r^2 + N_r^3 while the PCG products
+    fall slowly with N_r, and each product costs ~n^2 d, so larger N_r pays
+    only at the largest n."""
+    return int(min(n, 1024, max(math.ceil(2.0 * math.sqrt(n)), math.ceil(n / 64.0))))
 
 
 # Configurations of the workloads (sizes and field parameters).

@@ -157,7 +157,7 @@ def test_cccp_fit_matches_dense_oracle(L, ctx):
 
 
 def test_c1_end_to_end_fp64(L, ctx):
-    """Plain FP64 single instance (n=1024, d=16, lambda=1e-3, 3 Tx, N_r=128,
+    """Plain FP64 single instance (n=1024, d=16, lambda=1e-3, 3 Tx, N_r=64,
     PCG to 1e-8, 64x64 map).  kappa(A) ~ 1e6: the fit must match the dense
     oracle; the PCG arithmetic is checked on a fixed number of steps and alpha
     at tol 1e-10; at tol 1e-8 the stopping iteration is decided by rounding
@@ -436,7 +436,7 @@ def test_auto_variant_keeps_the_faster_product(L, ctx, n):
 
 
 def test_c1_stopping_index_five_seeds(L, ctx):
-    """The c1 configuration (n = 1024, d = 16, lambda = 1e-3, 3 Tx, N_r = 128,
+    """The c1 configuration (n = 1024, d = 16, lambda = 1e-3, 3 Tx, N_r = 64,
     tol 1e-8) on five seeds: the GPU's number of products lies within the
     oracle's own envelope of it (plain run, six summation-order permutations,
     six runs with per-apply noise at the measured difference between the
