@@ -448,6 +448,13 @@ def run_batched(args):
         h.copy_(a, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    # the same solves as concurrent single-instance solves on 16 streams
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, cinfos, _ = L.laker_pcg_solve_concurrent(ctx, items, tol, max_iter=20000, refine_every=20, streams=16,
+                                                allow_maxiter=True)
+    torch.cuda.synchronize()
+    conc_s = time.perf_counter() - t0
     # algorithmic HBM bytes of the solve: each product streams the float32 G
     # (n x ldk x 4 bytes); each float64-accurate residual streams the pair
     gbytes = 0.0
@@ -477,6 +484,10 @@ def run_batched(args):
                             "max": float(dn.max())},
         "iterations": {"p50": float(np.median(it)), "max": int(it.max()), "sum": int(it.sum())},
         "worst_rel_res_true": worst,
+        "concurrent_16_streams": {"solves_per_s": count / conc_s,
+                                  "converged": sum(int(f["converged"] == 1) for f in cinfos),
+                                  "worst_rel_res_true": max(f["rel_res_true"] for f in cinfos),
+                                  "note": "laker_pcg_solve_concurrent on the same instances, one call"},
         "e2e": {"value": count / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(sum(i.n for i in insts) * 8),
                 "d2h_bytes_per_step": int(sum(i.n for i in insts) * 8)},
         "gpu_launches": launches,
@@ -707,10 +718,12 @@ def run_combined(args):
     lambda log-uniform in [1e-5, 1e-2], 1-8 Tx).  A timed step takes
     `--combined-count` held-out instances of the same distribution through:
     * combined: float32 operators, the network's prediction used as Sigma_*
-      (no CCCP iteration), one persistent batched mixed PCG launch over all
-      instances; an instance that has not converged after `--combined-cap`
-      products falls back to a CCCP fit and a single solve (charged to the
-      step);
+      (no CCCP iteration), the solves of all instances together: concurrent
+      single-instance solves on 16 streams (`--combined-solver concurrent`,
+      the default, measured faster) or one persistent batched launch
+      (`batched`; the line reports the other solver's time too); an instance
+      that has not converged after `--combined-cap` products falls back to a
+      CCCP fit and a single solve (charged to the step);
     * mixed batched CCCP: the same, with CCCP fits;
     * plain float64: float64 operator, CCCP fit and PCG per instance, one at
       a time (the paper's method as printed)."""
@@ -756,7 +769,15 @@ def run_combined(args):
         phase_ms[name] = 1e3 * (t1 - t0)
         return t1
 
-    def combined_step(mode):
+    def solve_all(items, solver):
+        if solver == "concurrent":
+            return L.laker_pcg_solve_concurrent(ctx, items, tol, max_iter=args.combined_cap, refine_every=20,
+                                                streams=16, allow_maxiter=True)
+        return L.laker_pcg_solve_batched(ctx, items, tol, max_iter=args.combined_cap, refine_every=20,
+                                         allow_maxiter=True)
+
+    def combined_step(mode, solver=args.combined_solver):
+        phase_ms.clear()
         ops, precs = [], []
         t = time.perf_counter()
         for inst, (Q, y, Z, X) in zip(insts, ins):
@@ -769,9 +790,8 @@ def run_combined(args):
                 precs.append(L.laker_fit_preconditioner(ctx, op, Z))
         t = mark("precondition", t)
         items = [(op, P, y, None) for op, P, (_, y, _, _) in zip(ops, precs, ins)]
-        alphas, infos, _ = L.laker_pcg_solve_batched(ctx, items, tol, max_iter=args.combined_cap, refine_every=20,
-                                                    allow_maxiter=True)
-        t = mark("batched_solve", t)
+        alphas, infos, _ = solve_all(items, solver)
+        t = mark("solve_" + solver, t)
         fallback = 0
         if mode == "learned":
             for k, f in enumerate(infos):
@@ -818,6 +838,8 @@ def run_combined(args):
         s_l, (inf_l, fb, worst_l, ph_l) = timed(lambda: combined_step("learned"), args.steps)
     launches = ctx.launches() - launches0
     s_c, (inf_c, _, worst_c, ph_c) = timed(lambda: combined_step("cccp"), 1)
+    other = "batched" if args.combined_solver == "concurrent" else "concurrent"
+    s_o, (_, _, worst_o, ph_o) = timed(lambda: combined_step("learned", other), 1)
     s_p, (its_p, worst_p) = timed(plain_step, 1)
     line = {
         "metric": "solves/s at true rel-res 1e-6: mixed + batched + learned preconditioner vs plain FP64 PCG",
@@ -838,6 +860,9 @@ def run_combined(args):
         "plain_fp64": {"solves_per_s": count / s_p, "worst_rel_res_true": worst_p,
                        "pcg_products_mean": float(np.mean(its_p))},
         "speedup_vs_plain_fp64": s_p / s_l,
+        "solver": args.combined_solver,
+        "other_solver": {"solver": other, "solves_per_s": count / s_o, "worst_rel_res_true": worst_o,
+                         "phases_ms": ph_o},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
@@ -1062,6 +1087,7 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=2000)
     ap.add_argument("--combined-count", type=int, default=96)
     ap.add_argument("--combined-cap", type=int, default=4000)
+    ap.add_argument("--combined-solver", default="concurrent", choices=["concurrent", "batched"])
     ap.add_argument("--stream-m", type=int, default=512)
     ap.add_argument("--stream-steps", type=int, default=8)
     args = ap.parse_args()

@@ -84,7 +84,7 @@ typedef struct {
     double rel_res;      /* |r|/|y| of the recursive residual at exit */
     double rel_res_true; /* |y - (lambda I + G) alpha| / |y| (float64 operator) */
     int status;          /* laker_status of the solve */
-    int restarts;        /* mixed single solves: roll-backs of the replacement guard */
+    int restarts;        /* mixed single solves: roll-backs and direction restarts of the guard */
 } laker_solve_info;
 
 /* Context: binds a device and a CUDA stream (cudaStream_t passed as void*).
@@ -283,13 +283,14 @@ laker_status laker_precond_export(laker_ctx* ctx, const laker_precond* P, double
  *              by y - (lambda I + G) alpha computed with the float64-accurate
  *              operator, and the stop test uses that true residual.  0 = never.
  *              The replacements are guarded: the lowest true residual seen
- *              is kept with its iterate; a replacement more than 30 times
- *              above it, a product with p^T A p <= 0 or a non-finite
- *              residual roll alpha back to it, restart the direction and
- *              halve the interval (at least 4).  A roll-back at interval 4
- *              ends the solve with LAKER_ERR_MAXITER ("stagnated": the
- *              tolerance is below what the operator's accuracy lets the
- *              solve reach).
+ *              is kept with its iterate; a non-finite residual, or two
+ *              replacements in a row more than 30 times above the best,
+ *              roll alpha back to it, restart the direction and halve the
+ *              interval (at least 4); a product with p^T A p <= 0 forces a
+ *              replacement and restarts the direction.  A roll-back at
+ *              interval 4 ends the solve with LAKER_ERR_MAXITER
+ *              ("stagnated": the tolerance is below what the operator's
+ *              accuracy lets the solve reach).
  * alpha (device, n) receives the last iterate, also on LAKER_ERR_MAXITER
  *              (mixed forms: the iterate with the lowest true residual).
  */
@@ -440,6 +441,35 @@ typedef struct {
 laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batch_item* items,
                                      double tol, int max_iter, int refine_every,
                                      laker_solve_info* infos, double* done_ms);
+
+/*
+ * The same independent solves as laker_pcg_solve_batched, run as concurrent
+ * single-instance solves (laker_pcg_solve, Algorithm 1's PCG stage, one per
+ * instance): `streams` host threads each take the next instance and solve it
+ * on a stream of their own, so small instances overlap on the GPU and every
+ * instance stops on its own test without waiting for the others at a
+ * barrier (no counterpart in the paper).
+ *   items      host array of `count` instances, any precisions and variants
+ *              (laker_pcg_solve's rules per item).  An operator with a
+ *              matrix-free or packed-pair workspace (BF16X3, matrix-free
+ *              FP32) may appear in one item only.
+ *   streams    1 .. 64 worker threads and streams (at most count are used).
+ *   tol, max_iter, refine_every  as in laker_pcg_solve, for every instance.
+ *   infos      host array of `count` (may be NULL); done_ms (host, may be
+ *              NULL): host time from the call's start to each instance's end.
+ * The workers start after the work already queued on the context's stream and
+ * the call returns when every solve has ended.  Workspaces for all workers
+ * are allocated before the first solve and freed after the last; the solves
+ * themselves allocate nothing (an allocation or a free would synchronise the
+ * device and serialise the streams).
+ * Errors: LAKER_ERR_ARG for bad arguments or a shared workspace operator;
+ * LAKER_ERR_NONFINITE for a non-finite y; otherwise the worst instance status
+ * (a hard error, then LAKER_ERR_BREAKDOWN, then LAKER_ERR_MAXITER), every
+ * alpha written and its info saying which failed.
+ */
+laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, const laker_batch_item* items, double tol,
+                                        int max_iter, int refine_every, int streams, laker_solve_info* infos,
+                                        double* done_ms);
 
 /*
  * Learned set-to-parameters network (no counterpart in the paper, whose only

@@ -74,6 +74,8 @@ __global__ void k_nonfinite(int64_t count, const double* __restrict__ x, int* fl
     if (i < count && !isfinite(x[i])) atomicExch(flag, 1);
 }
 
+}  // namespace
+
 // Returns LAKER_ERR_NONFINITE if any of x[0..count) is NaN/Inf.
 laker_status scan_finite(laker_ctx* ctx, const double* x, int64_t count) {
     int* flag = nullptr;
@@ -89,7 +91,6 @@ laker_status scan_finite(laker_ctx* ctx, const double* x, int64_t count) {
     return h ? set_error(ctx, LAKER_ERR_NONFINITE, "non-finite value in input") : LAKER_OK;
 }
 
-}  // namespace
 
 extern "C" {
 

@@ -95,16 +95,56 @@ __device__ __forceinline__ bool running(const BArgs& a, int i) {
     return *(volatile const int*)&a.sc[i].converged == 0;
 }
 
+// Per-CTA copies in shared memory: the instance of each of this CTA's row and
+// direction items (item k of the CTA is blockIdx.x + k gridDim.x), and the
+// running / true-residual-due flags of every instance, refreshed after each
+// step that can change them.  A phase then skips finished instances with a
+// shared-memory read instead of two dependent L2 loads per item.  Null
+// pointers: the batch is too large for the copies and the global arrays are
+// read.
+struct BLocal {
+    unsigned char* run;
+    unsigned char* tru;
+    int* rinst;
+    int* kinst;
+    int nrow, nk;
+};
+__device__ __forceinline__ bool run_ok(const BArgs& a, const BLocal& L, int i) {
+    return L.run ? L.run[i] != 0 : running(a, i);
+}
+__device__ __forceinline__ bool true_due(const BArgs& a, const BLocal& L, int i) {
+    return L.tru ? L.tru[i] != 0 : *(volatile const int*)&a.sc[i].need_true != 0;
+}
+__device__ __forceinline__ int row_of(const BArgs& a, const BLocal& L, int k, int64_t it) {
+    return L.rinst ? L.rinst[k] : a.row_inst[it];
+}
+__device__ __forceinline__ int dir_of(const BArgs& a, const BLocal& L, int k, int64_t it) {
+    return L.kinst ? L.kinst[k] : a.k_inst[it];
+}
+__device__ void refresh(const BArgs& a, const BLocal& L) {
+    if (L.run) {
+        for (int i = threadIdx.x; i < a.count; i += BT) {
+            L.run[i] = *(volatile const int*)&a.sc[i].converged == 0;
+            L.tru[i] = *(volatile const int*)&a.sc[i].need_true != 0;
+        }
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void finish(BScal& s, int code) {
     s.converged = code;
     s.t_done = globaltimer();
 }
 
-// Fixed-order sum of the per-item partials [p0, p0 + cnt) (one thread).
+// Fixed-order sum of the per-item partials [p0, p0 + cnt) by one warp: lane
+// L adds items L, L + 32, ..., then a butterfly; every lane gets the same
+// total.  (One thread walking the items made each per-instance step a chain
+// of L2 loads, ~128 of them at n = 4096.)
 __device__ __forceinline__ double sum_items(const double* part, int64_t p0, int cnt) {
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int k = 0; k < cnt; ++k) s += __ldcg(part + p0 + k);
-    return s;
+    for (int k = lane; k < cnt; k += 32) s += __ldcg(part + p0 + k);
+    return lk::warp_sum(s);
 }
 
 // Block-wide sum written as this item's partial.
@@ -116,9 +156,10 @@ __device__ __forceinline__ void item_partial(double v, double* part, int64_t ite
 // ---- phases ----------------------------------------------------------------
 
 // INIT rows: alpha = 0, r = y, partial |y|^2.
-__device__ void ph_init(const BArgs& a, double* red) {
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const BInst& I = a.inst[a.row_inst[it]];
+__device__ void ph_init(const BArgs& a, double* red, const BLocal& L) {
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const BInst& I = a.inst[row_of(a, L, kq, it)];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double yy = 0.0;
         for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
@@ -143,11 +184,12 @@ __device__ __forceinline__ void load4(const double* u, int64_t e, double* v) {
     v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
 }
 template <typename PT>
-__device__ void ph_utr(const BArgs& a) {
+__device__ void ph_utr(const BArgs& a, const BLocal& L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < a.k_items; it += gridDim.x) {
-        const int ii = a.k_inst[it];
-        if (!running(a, ii)) continue;
+    for (int kq = 0; kq < L.nk; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const int ii = dir_of(a, L, kq, it);
+        if (!run_ok(a, L, ii)) continue;
         const BInst& I = a.inst[ii];
         const int k = (int)(it - I.kit0) * KB + warp;
         if (k >= I.n_r) continue;
@@ -179,11 +221,12 @@ __device__ void ph_utr(const BArgs& a) {
 
 // z = P r and partial r^T z.
 template <typename PT>
-__device__ void ph_precond(const BArgs& a, double* red, double* ts) {
+__device__ void ph_precond(const BArgs& a, double* red, double* ts, const BLocal& L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const int ii = a.row_inst[it];
-        if (!running(a, ii)) continue;
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const int ii = row_of(a, L, kq, it);
+        if (!run_ok(a, L, ii)) continue;
         const BInst& I = a.inst[ii];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double rz = 0.0;
@@ -239,10 +282,11 @@ __device__ void ph_precond(const BArgs& a, double* red, double* ts) {
 }
 
 // p = z + beta p (beta = 0 on the first pass), float32 copy for the product.
-__device__ void ph_newdir(const BArgs& a, bool first) {
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const int ii = a.row_inst[it];
-        if (!running(a, ii)) continue;
+__device__ void ph_newdir(const BArgs& a, bool first, const BLocal& L) {
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const int ii = row_of(a, L, kq, it);
+        if (!run_ok(a, L, ii)) continue;
         const BInst& I = a.inst[ii];
         const double beta = first ? 0.0 : __ldcg(&a.sc[ii].beta);
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
@@ -260,11 +304,12 @@ __device__ void ph_newdir(const BArgs& a, bool first) {
 __device__ __forceinline__ float dot4(const float4 k, const float4 p, float acc) {
     return fmaf(k.x, p.x, fmaf(k.y, p.y, fmaf(k.z, p.z, fmaf(k.w, p.w, acc))));
 }
-__device__ void ph_matvec(const BArgs& a, double* red) {
+__device__ void ph_matvec(const BArgs& a, double* red, const BLocal& L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const int ii = a.row_inst[it];
-        if (!running(a, ii)) continue;
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const int ii = row_of(a, L, kq, it);
+        if (!run_ok(a, L, ii)) continue;
         const BInst& I = a.inst[ii];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double pw = 0.0;
@@ -320,10 +365,11 @@ __device__ void ph_matvec(const BArgs& a, double* red) {
 }
 
 // alpha += delta p, r -= delta w, partial |r|^2.
-__device__ void ph_update(const BArgs& a, double* red) {
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const int ii = a.row_inst[it];
-        if (!running(a, ii)) continue;
+__device__ void ph_update(const BArgs& a, double* red, const BLocal& L) {
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const int ii = row_of(a, L, kq, it);
+        if (!run_ok(a, L, ii)) continue;
         const BInst& I = a.inst[ii];
         const double delta = __ldcg(&a.sc[ii].delta);
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
@@ -344,11 +390,12 @@ __device__ void ph_update(const BArgs& a, double* red) {
 // lambda = 1e-5): float64 products and sums keep the residual's noise two
 // orders below the 1e-6 test, where a split-float32 sum (2^-48 per term) does
 // not.  Two rows per warp share the loads of alpha.
-__device__ void ph_true(const BArgs& a, double* red) {
+__device__ void ph_true(const BArgs& a, double* red, const BLocal& L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const int ii = a.row_inst[it];
-        if (!running(a, ii) || !*(volatile const int*)&a.sc[ii].need_true) continue;
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const int ii = row_of(a, L, kq, it);
+        if (!run_ok(a, L, ii) || !true_due(a, L, ii)) continue;
         const BInst& I = a.inst[ii];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double rr = 0.0;
@@ -388,10 +435,11 @@ __device__ void ph_true(const BArgs& a, double* red) {
 
 // |y - (lambda I + G) alpha|^2 at float64 accuracy for every instance (the
 // reported true residual): float64 G, or hi + lo for mixed instances.
-__device__ void ph_final(const BArgs& a, double* red) {
+__device__ void ph_final(const BArgs& a, double* red, const BLocal& L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < a.row_items; it += gridDim.x) {
-        const BInst& I = a.inst[a.row_inst[it]];
+    for (int kq = 0; kq < L.nrow; ++kq) {
+        const int64_t it = blockIdx.x + (int64_t)kq * gridDim.x;
+        const BInst& I = a.inst[row_of(a, L, kq, it)];
         const int64_t i0 = (it - I.row0) * a.R, i1 = min(I.n, i0 + a.R);
         double rr = 0.0;
         for (int64_t i = i0 + warp; i < i1; i += BW) {
@@ -414,13 +462,19 @@ __device__ void ph_final(const BArgs& a, double* red) {
     }
 }
 
-// ---- per-instance scalar steps (one thread per instance) -------------------
+// ---- per-instance scalar steps (one warp per instance; lane 0 writes) ------
+
+__device__ __forceinline__ int warp_gid() { return (int)((blockIdx.x * (unsigned)BT + threadIdx.x) >> 5); }
+__device__ __forceinline__ int warp_count() { return (int)(gridDim.x * (unsigned)BW); }
 
 __device__ void sc_init(const BArgs& a, double tol) {
-    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    for (int i = warp_gid(); i < a.count; i += warp_count()) {
         const BInst& I = a.inst[i];
+        const double yy = sum_items(a.part, I.row0, I.rows);
+        if (!lead) continue;
         BScal& s = a.sc[i];
-        s.yy = sum_items(a.part, I.row0, I.rows);
+        s.yy = yy;
         s.tol2yy = tol * tol * s.yy;
         s.iters = 0;
         s.true_count = 0;
@@ -433,11 +487,13 @@ __device__ void sc_init(const BArgs& a, double tol) {
 }
 
 __device__ void sc_rz(const BArgs& a, bool first) {
-    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    for (int i = warp_gid(); i < a.count; i += warp_count()) {
         if (!running(a, i)) continue;
         const BInst& I = a.inst[i];
-        BScal& s = a.sc[i];
         const double tot = sum_items(a.part, I.row0, I.rows);
+        if (!lead) continue;
+        BScal& s = a.sc[i];
         if (!isfinite(tot) || tot < 0.0) { finish(s, 2); continue; }
         if (tot == 0.0) { finish(s, 1); continue; }
         s.beta = (!first && s.rz > 0.0) ? tot / s.rz : 0.0;
@@ -446,11 +502,13 @@ __device__ void sc_rz(const BArgs& a, bool first) {
 }
 
 __device__ void sc_delta(const BArgs& a) {
-    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    for (int i = warp_gid(); i < a.count; i += warp_count()) {
         if (!running(a, i)) continue;
         const BInst& I = a.inst[i];
-        BScal& s = a.sc[i];
         const double pAp = sum_items(a.part, I.row0, I.rows);
+        if (!lead) continue;
+        BScal& s = a.sc[i];
         s.pAp = pAp;
         s.iters += 1;
         if (!(pAp > 0.0) || !isfinite(pAp)) { s.delta = 0.0; finish(s, 2); continue; }
@@ -459,11 +517,13 @@ __device__ void sc_delta(const BArgs& a) {
 }
 
 __device__ void sc_stop(const BArgs& a, int* need_cnt) {
-    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    for (int i = warp_gid(); i < a.count; i += warp_count()) {
         if (!running(a, i)) continue;
         const BInst& I = a.inst[i];
-        BScal& s = a.sc[i];
         const double tot = sum_items(a.part, I.row0, I.rows);
+        if (!lead) continue;
+        BScal& s = a.sc[i];
         s.rr = tot;
         const bool small = tot <= s.tol2yy;
         if (!isfinite(tot)) {
@@ -479,12 +539,14 @@ __device__ void sc_stop(const BArgs& a, int* need_cnt) {
 }
 
 __device__ void sc_true(const BArgs& a) {
-    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    for (int i = warp_gid(); i < a.count; i += warp_count()) {
         if (!running(a, i)) continue;
-        BScal& s = a.sc[i];
-        if (!s.need_true) continue;
+        if (!*(volatile const int*)&a.sc[i].need_true) continue;
         const BInst& I = a.inst[i];
         const double tot = sum_items(a.part, I.row0, I.rows);
+        if (!lead) continue;
+        BScal& s = a.sc[i];
         s.rr = tot;
         s.rr_true = tot;
         s.true_count += 1;
@@ -496,9 +558,11 @@ __device__ void sc_true(const BArgs& a) {
 }
 
 __device__ void sc_final(const BArgs& a) {
-    for (int i = blockIdx.x * BT + threadIdx.x; i < a.count; i += gridDim.x * BT) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    for (int i = warp_gid(); i < a.count; i += warp_count()) {
         const BInst& I = a.inst[i];
-        a.sc[i].rr_true = sum_items(a.part, I.row0, I.rows);
+        const double tot = sum_items(a.part, I.row0, I.rows);
+        if (lead) a.sc[i].rr_true = tot;
     }
 }
 
@@ -509,55 +573,75 @@ __device__ void count_active(const BArgs& a, int* active) {
 
 template <typename PT>
 __global__ void __launch_bounds__(BT)
-k_batch_pcg(BArgs a, double tol) {
+k_batch_pcg(BArgs a, double tol, int local) {
     __shared__ double red[BW];
     __shared__ double ts[LK_MAX_NR];
+    extern __shared__ __align__(16) unsigned char b_smem[];
     BGlobal* g = a.g;
     int* err = &g->err;
     auto sync = [&]() { return lk::grid_sync(&g->gs, err, a.spin); };
+    // this CTA's items and, with local = 1, their shared-memory copies
+    BLocal L{};
+    L.nrow = a.row_items > blockIdx.x ? (int)((a.row_items - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+    L.nk = a.k_items > blockIdx.x ? (int)((a.k_items - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+    if (local) {
+        L.rinst = reinterpret_cast<int*>(b_smem);
+        L.kinst = L.rinst + L.nrow;
+        L.run = reinterpret_cast<unsigned char*>(L.kinst + L.nk);
+        L.tru = L.run + a.count;
+        for (int k = threadIdx.x; k < L.nrow; k += BT) L.rinst[k] = a.row_inst[blockIdx.x + (int64_t)k * gridDim.x];
+        for (int k = threadIdx.x; k < L.nk; k += BT) L.kinst[k] = a.k_inst[blockIdx.x + (int64_t)k * gridDim.x];
+        __syncthreads();
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) g->t0 = globaltimer();
-    ph_init(a, red);
+    ph_init(a, red, L);
     if (!sync()) return;
     sc_init(a, tol);
     if (!sync()) return;
-    ph_utr<PT>(a);
+    refresh(a, L);
+    ph_utr<PT>(a, L);
     if (!sync()) return;
-    ph_precond<PT>(a, red, ts);
+    ph_precond<PT>(a, red, ts, L);
     if (!sync()) return;
     sc_rz(a, true);
     if (!sync()) return;
-    ph_newdir(a, true);
+    refresh(a, L);
+    ph_newdir(a, true, L);
     if (blockIdx.x == 0 && threadIdx.x == 0) { g->active[0] = 0; g->need_true[0] = 0; }
     if (!sync()) return;
     for (int iter = 0;; ++iter) {
         const int par = iter & 1;
-        ph_matvec(a, red);
+        ph_matvec(a, red, L);
         if (!sync()) return;
         sc_delta(a);
         if (blockIdx.x == 0 && threadIdx.x == 0) { g->active[par ^ 1] = 0; g->need_true[par ^ 1] = 0; }
         if (!sync()) return;
-        ph_update(a, red);
+        refresh(a, L);
+        ph_update(a, red, L);
         if (!sync()) return;
         sc_stop(a, &g->need_true[par]);
         if (!sync()) return;
+        refresh(a, L);
         if (*(volatile int*)&g->need_true[par] > 0) {
-            ph_true(a, red);
+            ph_true(a, red, L);
             if (!sync()) return;
             sc_true(a);
             if (!sync()) return;
+            refresh(a, L);
         }
-        ph_utr<PT>(a);
+        ph_utr<PT>(a, L);
         if (!sync()) return;
-        ph_precond<PT>(a, red, ts);
+        ph_precond<PT>(a, red, ts, L);
         if (!sync()) return;
         sc_rz(a, false);
         count_active(a, &g->active[par]);
         if (!sync()) return;
         if (*(volatile int*)&g->active[par] == 0) break;
-        ph_newdir(a, false);
+        refresh(a, L);
+        ph_newdir(a, false, L);
         if (!sync()) return;
     }
-    ph_final(a, red);
+    ph_final(a, red, L);
     if (!sync()) return;
     sc_final(a);
 }
@@ -621,16 +705,23 @@ static laker_status batch_launch(laker_ctx* ctx, const std::vector<BInst>& hin, 
     a.mixed = fp64_prec ? 0 : 1;
     a.spin = ctx->wait_cycles > 0 ? (long long)ctx->wait_cycles : lk::GRID_SPIN_CYCLES;
     const void* fn = fp64_prec ? (const void*)k_batch_pcg<double> : (const void*)k_batch_pcg<float>;
+    // shared-memory copies of each CTA's item lists and of the instance flags,
+    // sized for the smallest grid this launch may take (one CTA per SM)
+    const int64_t per_cta = (a.row_items + ctx->num_sms - 1) / ctx->num_sms + (a.k_items + ctx->num_sms - 1) / ctx->num_sms;
+    const size_t lbytes = (size_t)per_cta * sizeof(int) + 2 * (size_t)count;
+    int local = lbytes <= (size_t)32768 ? 1 : 0;
+    const size_t smem = local ? (lbytes + 15) / 16 * 16 : 0;
+    LK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    LK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT, 0));
+    LK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT, smem));
     if (occ < 1) { cleanup(); return set_error(ctx, LAKER_ERR_CUDA, "batched kernel cannot be resident"); }
     const int grid = std::min(per_sm, occ) * ctx->num_sms;
-    void* args[] = {&a, &tol};
+    void* args[] = {&a, &tol, &local};
     cudaEvent_t e0, e1;
     LK_CUDA(ctx, cudaEventCreate(&e0));
     LK_CUDA(ctx, cudaEventCreate(&e1));
     LK_CUDA(ctx, cudaEventRecord(e0, s));
-    LK_CUDA(ctx, cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BT), args, 0, s));
+    LK_CUDA(ctx, cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BT), args, smem, s));
     LK_LAUNCHED(ctx);
     LK_CUDA(ctx, cudaEventRecord(e1, s));
     LK_CUDA(ctx, cudaEventSynchronize(e1));

@@ -73,20 +73,27 @@ struct GridSync {
     unsigned int gen;
 };
 constexpr long long GRID_SPIN_CYCLES = 4000000000ll;
+// Arrival is one acq_rel atomic on the counter (release: everything the CTA
+// wrote before the bar.sync that precedes it; acquire: the arrivals before
+// it), the last arrival resets the counter and publishes the next generation
+// with a release store, and the others poll it with acquire loads; no full
+// fences.  The generation is read before arriving, so it is this barrier's.
 __device__ __forceinline__ bool grid_sync(GridSync* gs, int* err, long long budget = GRID_SPIN_CYCLES) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* genp = &gs->gen;
-        const unsigned int g = *genp;
-        __threadfence();
-        if (atomicAdd(&gs->count, 1u) == gridDim.x - 1) {
-            atomicExch(&gs->count, 0u);
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
+        unsigned int g, prev;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gs->gen) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&gs->count) : "memory");
+        if (prev == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&gs->count), "r"(0u) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&gs->gen), "r"(g + 1u) : "memory");
         } else {
             const long long t0 = clock64();
-            for (unsigned int spins = 1; *genp == g; ++spins) {
+            for (unsigned int spins = 1;; ++spins) {
+                unsigned int cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&gs->gen) : "memory");
+                if (cur != g) break;
                 if ((spins & 63u) == 0) {
                     if (*(volatile int*)err) break;
                     if (clock64() - t0 > budget) {
@@ -96,7 +103,6 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int* err, long long budg
                 }
             }
         }
-        __threadfence();
         ok_s = (*(volatile int*)err == 0);
     }
     __syncthreads();

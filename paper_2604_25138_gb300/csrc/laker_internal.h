@@ -40,7 +40,8 @@ struct PcgScalars {
     int guard_action;   // 1: save alpha, r as the best iterate; 2: restore them
     int restart_dir;    // 1: the next direction is the preconditioned residual (beta = 0)
     int breakdown;      // p^T A p <= 0 in a mixed solve: replace and roll back
-    int pad3, pad4;
+    int grow;           // replacements in a row more than 30x above the best
+    int pad3;
 };
 
 struct laker_ctx {
@@ -135,10 +136,27 @@ laker_status copy_packed_tiles(laker_ctx* ctx, const float* src, int nb_src, flo
 laker_status op_matvec_inner(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
 laker_status op_matvec_fp64(laker_ctx* ctx, const laker_op* op, const double* x, double* w);
 // laker_pcg.cu
+// Preallocated buffers for solves that must not allocate (concurrent solves
+// on several streams: an allocation or free would synchronise the device).
+struct PcgArena {
+    double* base = nullptr;        // 8 n_cap doubles
+    int64_t n_cap = 0;
+    double* partials = nullptr;
+    int64_t partials_cap = 0;
+    void* t = nullptr;             // t_cap doubles
+    int64_t t_cap = 0;
+    PcgScalars* sc = nullptr;
+    int* flag_host = nullptr;      // pinned
+};
+// LAKER_ERR_NONFINITE if any of x[0..count) (device) is NaN or Inf
+laker_status scan_finite(laker_ctx* ctx, const double* x, int64_t count);
+laker_status pcg_arena_alloc(laker_ctx* ctx, int64_t n_max, int nw_max, PcgArena* a);
+void pcg_arena_free(PcgArena* a);
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P,
                        const double* y, double* alpha, double tol, int max_iter,
                        int refine_every, laker_solve_info* info, double* trace = nullptr,
-                       int trace_cap = 0, double R_ref = 0.0, double gap_tol = 0.0, bool warm = false);
+                       int trace_cap = 0, double R_ref = 0.0, double gap_tol = 0.0, bool warm = false,
+                       const PcgArena* arena = nullptr);
 laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double* r, double* z);
 // laker_fit.cu
 laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,

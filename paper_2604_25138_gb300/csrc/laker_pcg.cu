@@ -430,15 +430,23 @@ k_pcg_update(int64_t n, const double* __restrict__ p, const double* __restrict__
 // diverged on that instance after reaching 1.2e-6, every 20 converged.  The
 // recursive residual itself stays within ~1e-3 of the true one at every
 // replacement, so the guard watches the true residual: the lowest one seen is
-// saved with its iterate; a replacement 30 times above it (healthy solves stay
-// within ~3 times of their running best once past the first replacement), a
-// breakdown p^T A~ p <= 0 or a non-finite residual roll back to the saved
-// iterate, restart the direction and halve the interval.  At the smallest
+// saved with its iterate; a non-finite residual, or two replacements in a row
+// more than 30 times above the best, roll back to the saved iterate, restart
+// the direction and halve the interval.  (CG's residual is not monotone: its
+// early transient stays within ~4 times of the first replacement's value, and
+// near the accuracy floor single spikes above 30 times recover -- a float32
+// solve at lambda = 1.1e-5, n = 7633 that rolled back on each spike ended as
+// stagnated, where the unguarded iteration converged -- while divergence
+// grows at every replacement.)  A breakdown p^T A~ p <= 0 only makes the
+// direction useless: it forces a replacement and restarts the direction from
+// the current iterate, or rolls back at once if that replacement is more than
+// 30 times above the best.  At the smallest
 // interval a further roll-back ends the solve (stagnation).  (The true energy
 // phi(alpha), exact CG's monotone quantity, cannot serve: near convergence its
 // changes are below the cancellation of y^T alpha in float64.)
 constexpr int GUARD_MIN_INTERVAL = 4;
 constexpr double GUARD_GROWTH2 = 900.0;   // (30x)^2 in |r|^2
+constexpr int GUARD_RISES = 2;             // ... at that many replacements in a row
 
 __global__ void __launch_bounds__(VEC_THREADS)
 k_true_residual(int64_t n, const double* __restrict__ y, const double* __restrict__ w2, double* __restrict__ r,
@@ -469,16 +477,27 @@ k_true_residual(int64_t n, const double* __restrict__ y, const double* __restric
                 sc->converged = 1;
             } else if (!bad && tot < sc->rr_best) {
                 sc->rr_best = tot;
+                sc->grow = 0;
                 action = 1;
-                if (sc->breakdown) sc->restart_dir = 1;   // keep the iterate, drop the direction
-            } else if (bad || sc->breakdown || tot > GUARD_GROWTH2 * sc->rr_best) {
+                if (sc->breakdown) {   // keep the iterate, drop the direction
+                    sc->restart_dir = 1;
+                    sc->restarts += 1;
+                }
+            } else if (bad || (tot > GUARD_GROWTH2 * sc->rr_best && (++sc->grow >= GUARD_RISES || sc->breakdown))) {
                 action = 2;
+                sc->grow = 0;
                 if (sc->interval <= GUARD_MIN_INTERVAL) {
                     sc->converged = 4;   // stagnated: the saved iterate is returned
                 } else {
                     sc->interval = max(GUARD_MIN_INTERVAL, sc->interval / 2);
                     sc->restarts += 1;
                     sc->restart_dir = 1;
+                }
+            } else {
+                if (tot <= GUARD_GROWTH2 * sc->rr_best) sc->grow = 0;
+                if (sc->breakdown) {   // no roll-back due: drop only the direction
+                    sc->restart_dir = 1;
+                    sc->restarts += 1;
                 }
             }
             sc->breakdown = 0;
@@ -762,6 +781,7 @@ struct Workspace {
     int vec_blocks;
     int pre_blocks;
     int mv_blocks;
+    bool borrowed;   // buffers belong to a PcgArena: nothing to free
 };
 
 // Elementwise vector kernels with a scalar reduction.
@@ -872,7 +892,32 @@ laker_status ws_alloc(laker_ctx* ctx, const laker_op* op, int n_r, Workspace& ws
     ws.ticket = ws.sc->ticket + 7;
     return LAKER_OK;
 }
+// Workspace on an arena's buffers (no allocation); LAKER_ERR_ARG if the solve
+// does not fit the arena's capacities.
+laker_status ws_borrow(laker_ctx* ctx, const laker_op* op, int n_r, const PcgArena& a, Workspace& ws) {
+    const int64_t n = op->n;
+    const int64_t nb = std::max<int64_t>(8 * ctx->num_sms + 8, 4 * ((n + 127) / 128) + 8);
+    const int nr = std::max(1, n_r);
+    const int64_t tneed = (int64_t)nr * utr_chunks(ctx, n, nr);
+    if (n > a.n_cap || nb > a.partials_cap || tneed > a.t_cap)
+        return set_error(ctx, LAKER_ERR_ARG, "solve larger than the workspace arena");
+    ws.vec_blocks = vec_blocks_for(ctx, n);
+    ws.pre_blocks = pre_blocks_for(ctx, n);
+    ws.mv_blocks = mv_blocks_for(ctx, n);
+    double* base = a.base;
+    ws.r = base; ws.z = base + n; ws.p[0] = base + 2 * n; ws.p[1] = base + 3 * n; ws.w = base + 4 * n;
+    ws.w2 = base + 5 * n; ws.abest = base + 6 * n; ws.rbest = base + 7 * n;
+    ws.partials = a.partials;
+    ws.t = a.t;
+    ws.sc = a.sc;
+    LK_CUDA(ctx, cudaMemsetAsync(ws.sc, 0, sizeof(PcgScalars), ctx->stream));
+    ws.ticket = ws.sc->ticket + 7;
+    ws.borrowed = true;
+    return LAKER_OK;
+}
+
 void ws_free(Workspace& ws) {
+    if (ws.borrowed) return;
     cudaFree(ws.r);
     cudaFree(ws.partials);
     cudaFree(ws.t);
@@ -993,6 +1038,29 @@ laker_status op_time_product(laker_ctx* ctx, const laker_op* op, const double* x
     return mf ? mf_status(ctx, op) : LAKER_OK;
 }
 
+laker_status pcg_arena_alloc(laker_ctx* ctx, int64_t n_max, int nw_max, PcgArena* a) {
+    *a = PcgArena{};
+    a->n_cap = std::max<int64_t>(1, n_max);
+    a->partials_cap = std::max<int64_t>(8 * ctx->num_sms + 8, 4 * ((a->n_cap + 127) / 128) + 8);
+    a->t_cap = (int64_t)std::max(1, nw_max) * 32;   // utr_chunks() <= 32
+    laker_status st;
+    if ((st = lk_malloc(ctx, (void**)&a->base, (size_t)8 * a->n_cap * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&a->partials, (size_t)a->partials_cap * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, &a->t, (size_t)a->t_cap * sizeof(double))) != LAKER_OK) return st;
+    if ((st = lk_malloc(ctx, (void**)&a->sc, sizeof(PcgScalars))) != LAKER_OK) return st;
+    LK_CUDA(ctx, cudaMallocHost(&a->flag_host, sizeof(int)));
+    return LAKER_OK;
+}
+
+void pcg_arena_free(PcgArena* a) {
+    cudaFree(a->base);
+    cudaFree(a->partials);
+    cudaFree(a->t);
+    cudaFree(a->sc);
+    if (a->flag_host) cudaFreeHost(a->flag_host);
+    *a = PcgArena{};
+}
+
 laker_status pcg_prepare(laker_ctx* ctx) {
     LK_CUDA(ctx, cudaFuncSetAttribute(k_matvec_mat<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)MV_SMEM_MAX));
@@ -1041,12 +1109,13 @@ laker_status precond_apply(laker_ctx* ctx, const laker_precond* P, const double*
 
 laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* P, const double* y,
                        double* alpha, double tol, int max_iter, int refine_every, laker_solve_info* info,
-                       double* trace, int trace_cap, double R_ref, double gap_tol, bool warm) {
+                       double* trace, int trace_cap, double R_ref, double gap_tol, bool warm,
+                       const PcgArena* arena) {
     const int64_t n = op->n;
     const bool mixed = (op->precision != LAKER_FP64) && refine_every > 0;
     const bool use32 = (op->precision != LAKER_FP64);
     Workspace ws{};
-    laker_status st = ws_alloc(ctx, op, P ? P->n_w : 0, ws);
+    laker_status st = arena ? ws_borrow(ctx, op, P ? P->n_w : 0, *arena, ws) : ws_alloc(ctx, op, P ? P->n_w : 0, ws);
     if (st != LAKER_OK) return st;
     PrecView pv = make_view(ctx, P, use32);
     if (P && P->kind == PRECOND_CCCP && ((use32 && (P->UT32 == nullptr || P->W32 == nullptr)) ||
@@ -1124,7 +1193,8 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     if (ce != cudaSuccess) { cudaGraphDestroy(graph); ws_free(ws); return set_error(ctx, LAKER_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
 
     int* flag_host = nullptr;
-    LK_CUDA(ctx, cudaMallocHost(&flag_host, sizeof(int)));
+    if (arena) flag_host = arena->flag_host;
+    else LK_CUDA(ctx, cudaMallocHost(&flag_host, sizeof(int)));
     const int max_replays = max_iter / (2 * H) + 2;
     for (int rep = 0; rep < max_replays; ++rep) {
         LK_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
@@ -1135,7 +1205,7 @@ laker_status pcg_solve(laker_ctx* ctx, const laker_op* op, const laker_precond* 
     }
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
-    cudaFreeHost(flag_host);
+    if (!arena) cudaFreeHost(flag_host);
     if (op->variant == LAKER_MATRIX_FREE && (st = mf_status(ctx, op)) != LAKER_OK) { ws_free(ws); return st; }
     if ((st = resid_status(ctx, op)) != LAKER_OK) { ws_free(ws); return st; }
 

@@ -116,6 +116,8 @@ def library() -> ctypes.CDLL:
         "laker_setnet_save": (i32, [vp, vp, ctypes.c_char_p]),
         "laker_setnet_load": (i32, [vp, ctypes.c_char_p, pvp]),
         "laker_op_append": (i32, [vp, vp, vp, i64, pvp]),
+        "laker_pcg_solve_concurrent": (i32, [vp, i32, ctypes.POINTER(BatchItem), f64, i32, i32, i32,
+                                             ctypes.POINTER(SolveInfo), ctypes.POINTER(f64)]),
         "laker_pcg_solve_warm": (i32, [vp, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(SolveInfo)]),
         "laker_fit_preconditioner_warm": (i32, [vp, vp, vp, i32, f64, f64, f64, i32, f64, vp, pvp,
                                                 ctypes.POINTER(FitInfo)]),
@@ -545,6 +547,30 @@ def laker_pcg_solve_batched(ctx: Context, items, tol: float, max_iter: int = 100
     done = (ctypes.c_double * count)()
     with ctx:
         st = library().laker_pcg_solve_batched(ctx.handle, count, arr, tol, max_iter, refine_every, infos, done)
+    ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+    return (alphas, [{f: getattr(infos[k], f) for f, _ in SolveInfo._fields_} for k in range(count)],
+            [done[k] for k in range(count)])
+
+
+def laker_pcg_solve_concurrent(ctx: Context, items, tol: float, max_iter: int = 100000, refine_every: int = 0,
+                               streams: int = 16, allow_maxiter: bool = False):
+    """items: sequence of (op, P or None, y, alpha or None), solved as concurrent
+    single-instance solves on `streams` streams.  Returns the list of alphas,
+    the list of info dicts and the per-instance end times in ms (host clock)."""
+    count = len(items)
+    arr = (BatchItem * count)()
+    alphas = []
+    for k, (op, P, y, alpha) in enumerate(items):
+        if alpha is None:
+            alpha = torch.empty_like(y)
+        alphas.append(alpha)
+        arr[k] = BatchItem(op.handle, P.handle if P is not None else None, _ptr(y, "y", op.n),
+                           _ptr(alpha, "alpha", op.n))
+    infos = (SolveInfo * count)()
+    done = (ctypes.c_double * count)()
+    with ctx:
+        st = library().laker_pcg_solve_concurrent(ctx.handle, count, arr, tol, max_iter, refine_every, streams,
+                                                  infos, done)
     ctx.check(st, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
     return (alphas, [{f: getattr(infos[k], f) for f, _ in SolveInfo._fields_} for k in range(count)],
             [done[k] for k in range(count)])
