@@ -56,6 +56,13 @@ struct MfCfg {
     static constexpr int STAGES = DPAD >= 64 ? 4 : 8;      // ring of streamed j-block operand tiles
     static constexpr int TILE_BYTES = MF_B * DPAD * 2;     // one bf16 operand tile (128 rows)
     static constexpr int SWZ = DPAD * 2;                    // swizzle span = row bytes
+    // add the four epilogue parts of a column sum in shared memory (one
+    // partial per column and tile) or write them apart (four): with d = 64 the
+    // tensor cores leave the epilogue slack for the extra barrier and the
+    // partials shrink 4x (n = 65536: 0.54 GB of partial writes and reads per
+    // product; the product measured 934 -> 900 us); at d <= 32 the epilogue is
+    // the bottleneck and the barrier made the main kernel 16 % slower
+    static constexpr bool REDUCE = DPAD >= 64;
 };
 
 struct MfSmem {
@@ -66,6 +73,8 @@ struct MfSmem {
     uint64_t bfull;
     uint64_t bempty;
     uint32_t tmem_base;
+    // column sums of the four epilogue parts of a lane quadrant, by tile parity
+    float cred[2][4][MF_EPW][32];
 };
 
 // Symmetric tile schedule.  With nb blocks of 128 indices, block row I owns
@@ -164,8 +173,8 @@ __device__ __forceinline__ void mf_tile_epilogue(uint32_t tcol, float2* acc, con
 // Epilogue warp (quadrant q, part h) owns lanes 32q..32q+31 and columns
 // 32h..32h+31: it accumulates the block-I row sums over its lanes in
 // registers for the whole segment, and writes the block-J sums of an
-// off-diagonal tile to colpart[(x * 128 + j) * MF_EPW + h] (the four parts of a
-// column are one 16-byte load for the finishing kernel).  At the end of a
+// off-diagonal tile to colpart: added over the four parts h in shared memory
+// to colpart[x * 128 + j] (d = 64), or apart to colpart[(x * 128 + j) * 4 + h].  At the end of a
 // segment the row sums are reduced over the lanes and stored to
 // rowpart[((I * slots + slot) * 4 + q) * 128 + i].
 template <int DPAD>
@@ -334,8 +343,22 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S->tempty[accb]);
-            if (!diag)
-                colpart[((t0 + it) * MF_B + q * 32 + lane) * MF_EPW + h] = (sJ[0].x + sJ[0].y) + (sJ[1].x + sJ[1].y);
+            if (!diag) {
+                const float part = (sJ[0].x + sJ[0].y) + (sJ[1].x + sJ[1].y);
+                if (MfCfg<DPAD>::REDUCE) {
+                    // the quadrant's four parts of a column are added in shared
+                    // memory, in a fixed order, and written once: a quarter of
+                    // the partial traffic of writing them apart
+                    float(*cr)[32] = S->cred[it & 1][q];
+                    cr[h][lane] = part;
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(32 * MF_EPW) : "memory");
+                    if (h == 0)
+                        colpart[(t0 + it) * MF_B + q * 32 + lane] =
+                            (cr[0][lane] + cr[1][lane]) + (cr[2][lane] + cr[3][lane]);
+                } else {
+                    colpart[((t0 + it) * MF_B + q * 32 + lane) * MF_EPW + h] = part;
+                }
+            }
             I = In;
             k = kn;
         }
@@ -373,12 +396,13 @@ __global__ void k_mf_prep(int64_t n, int64_t npad, const double* __restrict__ pi
 // the row partials; the groups are added in a fixed order.  p^T w -> delta in
 // the last CTA.
 constexpr int MF_FIN_COLS = 32;
-static_assert(MF_EPW == 4, "the finishing kernel reads the four epilogue parts of a column as one float4");
+static_assert(MF_EPW == 4, "the epilogue adds the four parts of a column in shared memory");
 constexpr int MF_FIN_GROUPS = 16;
 __global__ void __launch_bounds__(MF_FIN_GROUPS * MF_FIN_COLS)
 k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ rowpart,
-            const float* __restrict__ colpart, const int* __restrict__ nslots, const double* __restrict__ p,
-            double* __restrict__ w, PcgScalars* sc, double* __restrict__ partials, const int* err) {
+            const float* __restrict__ colpart, int parts, const int* __restrict__ nslots,
+            const double* __restrict__ p, double* __restrict__ w, PcgScalars* sc, double* __restrict__ partials,
+            const int* err) {
     if (sc != nullptr && *(volatile const int*)&sc->converged) return;
     __shared__ double red[MF_FIN_GROUPS * MF_FIN_COLS / 32];
     __shared__ float gsum[MF_FIN_GROUPS][MF_FIN_COLS];
@@ -392,21 +416,31 @@ k_mf_finish(int64_t n, MfSched sch, double lambda, const float* __restrict__ row
         for (int e = grp; e < 4 * nslot; e += MF_FIN_GROUPS)
             s += __ldg(rowpart + (((int64_t)I * sch.slots + e / 4) * 4 + (e % 4)) * MF_B + c);
     }
-    // column sums of the tiles (I - kk, I): four independent 16-byte loads in flight
+    // column sums of the tiles (I - kk, I): four independent loads in flight;
+    // parts = 4: the epilogue's four parts of a column are one 16-byte load,
+    // added in the epilogue's order
     float t[2] = {0.f, 0.f};
     const float4* cp4 = reinterpret_cast<const float4*>(colpart);
     for (int kb = 1 + grp; kb <= sch.base; kb += 4 * MF_FIN_GROUPS) {
-        float4 v[4];
+        float v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int kk = kb + u * MF_FIN_GROUPS;
             int Ip = I - kk;
             if (Ip < 0) Ip += sch.nb;
             const bool ok = kk <= sch.base && kk < mf_row_len(Ip, sch);
-            v[u] = ok ? __ldg(cp4 + (mf_row_start(Ip, sch) + kk) * MF_B + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int64_t x = (mf_row_start(Ip, sch) + kk) * MF_B + c;
+            if (!ok) {
+                v[u] = 0.f;
+            } else if (parts == 1) {
+                v[u] = __ldg(colpart + x);
+            } else {
+                const float4 q4 = __ldg(cp4 + x);
+                v[u] = (q4.x + q4.y) + (q4.z + q4.w);
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) t[u & 1] += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+        for (int u = 0; u < 4; ++u) t[u & 1] += v[u];
     }
     gsum[grp][threadIdx.x % MF_FIN_COLS] = s + (t[0] + t[1]);
     __syncthreads();
@@ -512,7 +546,7 @@ laker_status mf_prepare(laker_ctx* ctx, laker_op* op) {
     if ((st = lk_malloc(ctx, (void**)&wk->pf, (size_t)npad * sizeof(float))) != LAKER_OK) { delete wk; return st; }
     if ((st = lk_malloc(ctx, (void**)&wk->rowpart, (size_t)sc.nb * sc.slots * 4 * MF_B * sizeof(float))) !=
         LAKER_OK) { mf_release_work(wk); return st; }
-    if ((st = lk_malloc(ctx, (void**)&wk->colpart, (size_t)sc.T * MF_EPW * MF_B * sizeof(float))) != LAKER_OK) {
+    if ((st = lk_malloc(ctx, (void**)&wk->colpart, (size_t)sc.T * (op->dpad >= 64 ? 1 : MF_EPW) * MF_B * sizeof(float))) != LAKER_OK) {
         mf_release_work(wk);
         return st;
     }
@@ -589,7 +623,7 @@ laker_status mf_matvec_launch(laker_ctx* ctx, const laker_op* op, const double* 
     LK_LAUNCHED(ctx);
     laker_status st = mf_launch_main(ctx, op, wk, sc);
     if (st != LAKER_OK) return st;
-    k_mf_finish<<<dim3(wk->sch.nb, MF_B / MF_FIN_COLS), MF_FIN_GROUPS * MF_FIN_COLS, 0, ctx->stream>>>(n, wk->sch, op->lambda, wk->rowpart, wk->colpart, wk->nslots, p, w, sc, partials,
+    k_mf_finish<<<dim3(wk->sch.nb, MF_B / MF_FIN_COLS), MF_FIN_GROUPS * MF_FIN_COLS, 0, ctx->stream>>>(n, wk->sch, op->lambda, wk->rowpart, wk->colpart, op->dpad >= 64 ? 1 : MF_EPW, wk->nslots, p, w, sc, partials,
                                              wk->err);
     LK_LAUNCHED(ctx);
     return LAKER_OK;
