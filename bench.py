@@ -552,7 +552,8 @@ def run_learned(args):
             conv = sum(int(r[k]["converged"] == 1) for r in sel)
             out[k] = {"pcg_iterations_mean": float(np.mean(it)), "fit_ms_mean": 1e3 * float(np.mean(fit)),
                       "solve_ms_mean": 1e3 * float(np.mean(sol)), "converged": conv,
-                      "solves_per_s": len(sel) / float(np.sum(fit) + np.sum(sol))}
+                      "solves_per_s": len(sel) / float(np.sum(fit) + np.sum(sol)),
+                      "kappa_PA_median": float(np.median([r[k]["kappa_PA"] for r in sel]))}
             if k in ("cccp", "warm"):
                 out[k]["cccp_iterations_mean"] = float(np.mean([r[k]["cccp_iterations"] for r in sel]))
         # learned with the fallback: CCCP's time and iterations are charged when it falls back

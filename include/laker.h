@@ -475,12 +475,14 @@ laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, const laker_b
  * Learned set-to-parameters network (no counterpart in the paper, whose only
  * learning is the CCCP fit of Sec. IV-B..D).  It reads an instance as a set of
  * points x_i = [location / L (2), q_i (d), y_i] and predicts log c and the
- * per-direction log D_k of Sigma_* = c I + U diag(D) U^T:
+ * per-direction log(D_k N_r / n) of Sigma_* = c I + U diag(D) U^T (both
+ * targets free of the instance size: tr Sigma_* = n):
  *   h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), h3 = tanh(h2 W3 + b3);
  *   z = mean over the points of h3;
  *   log c = tanh(z Wg1 + bg1) . wg2 + bg2;
- *   log D_k = tanh([z, f_k] Wd1 + bd1) . wd2 + bd2 with the direction
- *   features f_k = [log |u_k|, sum_j M_kj^2] (laker_precond_direction_features).
+ *   log(D_k N_r / n) = tanh([z, f_k] Wd1 + bd1) . wd2 + bd2 with the
+ *   direction features f_k = [log(|u_k| / n), (1/N_r) sum_j M_kj^2]
+ *   (laker_precond_direction_features; |u_k| before normalisation).
  * Loss over a batch of B instances:
  *   (1/B) sum_b [(log c_b - t_b)^2 + (1/K_b) sum_k (log D_bk - T_bk)^2].
  * Weights: float32 masters, used in bf16; float32 activations and sums; Adam
@@ -527,14 +529,15 @@ laker_status laker_setnet_gradient(laker_ctx* ctx, laker_setnet* net, int B, con
 laker_status laker_setnet_train_step(laker_ctx* ctx, laker_setnet* net, int B, const float* X, const int* poff,
                                      const float* F, const int* koff, const float* tc, const float* tD, float lr,
                                      float* loss);
-/* F (device, n_r x 2 float32) = [log |u_k|, sum_j M_kj^2] of a CCCP preconditioner's directions */
+/* F (device, n_r x 2 float32) = [log(|u_k| / n), (1/N_r) sum_j M_kj^2] of a CCCP preconditioner's directions */
 laker_status laker_precond_direction_features(laker_ctx* ctx, const laker_precond* P, float* F);
 /*
  * CCCP fit started from, or replaced by, the network's prediction (Sec. IV-D
  * iteration; the prediction is an extension beyond the paper).  After the
  * directions U and their Gram M are formed, the network predicts (c, D) from
  * the point features X (device, n x in_dim, laker_setnet_point_features) and
- * the direction features; the prediction is scaled to tr Sigma = n.
+ * the direction features; D_k = (n / N_r) exp(prediction), and (c, D) is
+ * scaled to tr Sigma = n.
  *   mode 0: CCCP iterations start from the prediction (warm start);
  *   mode 1: the prediction is used as Sigma_* (no CCCP iteration).
  * Other arguments as laker_fit_preconditioner.

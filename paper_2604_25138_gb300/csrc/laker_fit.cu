@@ -178,14 +178,17 @@ __global__ void k_colscale(int64_t n, int n_r, double* __restrict__ U, const dou
 
 // Direction features of the learned start: F[k] = [log |u_k|, sum_j M_kj^2]
 // (inv[k] = 1/|u_k| from k_colnorm; M the Gram of the unit directions).
-__global__ void k_dir_features(int nr, const double* __restrict__ inv, const double* __restrict__ M,
+// Scale-free direction features [log(|u_k| / n), (1/N_r) sum_j M_kj^2]:
+// |u_k| = |(lambda I + G) z_k| grows about like n and the row sums of M like
+// N_r, so the raw values tie the network to the training sizes.
+__global__ void k_dir_features(int nr, double n, const double* __restrict__ inv, const double* __restrict__ M,
                                float* __restrict__ F) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nr) return;
     double s = 0.0;
     for (int j = 0; j < nr; ++j) s = fma(M[(int64_t)k * nr + j], M[(int64_t)k * nr + j], s);
-    F[2 * k] = (float)(inv[k] > 0.0 ? -log(inv[k]) : 0.0);
-    F[2 * k + 1] = (float)s;
+    F[2 * k] = (float)(inv[k] > 0.0 ? -log(inv[k] * n) : 0.0);
+    F[2 * k + 1] = (float)(s / nr);
 }
 
 // ---------------------------------------------------------------------------
@@ -767,7 +770,7 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     if (rho < 0.0) rho = (nr >= n) ? 1e-3 : std::min(0.5, std::max(1e-3, gamma * (1.0 - (double)nr / n)));
     // direction features (inputs of the learned start, exported with P)
     if ((st = lk_malloc(ctx, (void**)&P->feat, (size_t)2 * nr * sizeof(float))) != LAKER_OK) return st;
-    k_dir_features<<<gsz(nr), 256, 0, s>>>(nr, tmpv, M, P->feat);
+    k_dir_features<<<gsz(nr), 256, 0, s>>>(nr, (double)n, tmpv, M, P->feat);
     LK_LAUNCHED(ctx);
     CccpState h{};
     h.c = 1.0;
@@ -786,8 +789,10 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
             LK_CUDA(ctx, cudaMemcpyAsync(&hc, logc, sizeof(float), cudaMemcpyDeviceToHost, s));
             LK_CUDA(ctx, cudaMemcpyAsync(hD.data(), logD, sizeof(float) * nr, cudaMemcpyDeviceToHost, s));
             LK_CUDA(ctx, cudaStreamSynchronize(s));
+            // the network predicts log c and the scale-free log(D_k N_r / n)
             c0 = std::exp((double)hc);
-            for (int k = 0; k < nr; ++k) D0[(size_t)k] = std::exp(std::min(50.0, (double)hD[(size_t)k]));
+            for (int k = 0; k < nr; ++k)
+                D0[(size_t)k] = std::exp(std::min(50.0, (double)hD[(size_t)k])) * (double)n / nr;
         } else {
             LK_CUDA(ctx, cudaMemcpyAsync(D0.data(), warm->D, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
             LK_CUDA(ctx, cudaStreamSynchronize(s));

@@ -1,14 +1,15 @@
 // Learned set-to-parameters network (an extension beyond the paper, whose
 // only learning is the CCCP fit of Sec. IV-B..D): predicts log c and the
-// per-direction log D_k of Sigma_* = c I + U diag(D) U^T for a new
+// per-direction log(D_k N_r / n) of Sigma_* = c I + U diag(D) U^T for a new
 // measurement set, to replace or start the CCCP fit.
 //
 //   per point:     h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), h3 = tanh(h2 W3 + b3)
 //                  with x = [location / L, q, y]
 //   set code:      z = mean over the points of h3
 //   log c:         g = tanh(z Wg1 + bg1), log c = g . wg2 + bg2
-//   direction k:   e_k = tanh([z, f_k] Wd1 + bd1), log D_k = e_k . wd2 + bd2,
-//                  f_k = [log |u_k|, sum_j M_kj^2] from the fit's first stage
+//   direction k:   e_k = tanh([z, f_k] Wd1 + bd1), log(D_k N_r / n) = e_k . wd2 + bd2,
+//                  f_k = [log(|u_k| / n), (1/N_r) sum_j M_kj^2] from the fit's first stage
+//                  (every input and target free of the instance size)
 //   loss:          (1/B) sum_b [(log c_b - t_b)^2 + (1/K_b) sum_k (log D_bk - T_bk)^2]
 //
 // Weights are used in bf16 (the rounding of float32 master weights, refreshed

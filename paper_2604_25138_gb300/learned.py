@@ -51,7 +51,8 @@ def fit_example(ctx, inst, precision=L.FP32, n_r=None, seed=0) -> Example:
     F = L.laker_precond_direction_features(ctx, P)
     X = instance_inputs(ctx, inst)
     ex = Example(X=X, F=F, logc=float(np.log(c)),
-                 logD=torch.log(torch.clamp(D, min=1e-30)).to(torch.float32), cccp_iterations=P.info["iterations"])
+                 logD=(torch.log(torch.clamp(D, min=1e-30)) + float(np.log(n_r / inst.n))).to(torch.float32),
+                 cccp_iterations=P.info["iterations"])
     P.close()
     op.close()
     return ex
@@ -76,8 +77,9 @@ def train(ctx, net, examples, steps: int, batch: int = 8, lr: float = 1e-3, seed
 
 
 def compare(ctx, net, inst, tol: float = 1e-6, precision=L.FP32, n_r=None, seed=0, refine_every: int = 20):
-    """PCG iterations and times for one instance under the cold CCCP fit, the
-    warm-started fit, the prediction used directly, Jacobi and none."""
+    """PCG iterations, times and the Lanczos estimate of kappa(P A) for one
+    instance under the cold CCCP fit, the warm-started fit, the prediction used
+    directly, Jacobi and none."""
     n_r = n_r or synth.default_num_directions(inst.n)
     op = L.laker_build_kernel(ctx, _dev(inst.Q), inst.scale, inst.lam, precision)
     Z = _dev(synth.directions(inst.n, n_r, seed))
@@ -95,9 +97,15 @@ def compare(ctx, net, inst, tol: float = 1e-6, precision=L.FP32, n_r=None, seed=
                                     allow_maxiter=True)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
+        # kappa(P A) from the Lanczos tridiagonal of an untimed traced solve
+        # (at most 2000 products: a lower estimate for the slow preconditioners)
+        _, _, tr = L.laker_pcg_solve_trace(ctx, op, P, y, tol, max_iter=2000, refine_every=refine_every,
+                                           allow_maxiter=True)
+        lo, hi = L.laker_lanczos_extremes(tr)
         out[name] = dict(fit_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"],
                          converged=info["converged"], rel_res_true=info["rel_res_true"],
-                         cccp_iterations=(P.info.get("iterations") if P is not None else 0))
+                         cccp_iterations=(P.info.get("iterations") if P is not None else 0),
+                         kappa_PA=(hi / lo) if lo > 0 else float("inf"))
         if P is not None:
             P.close()
 
