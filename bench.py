@@ -56,9 +56,11 @@ SINGLE = {
 # ~12 s at n = 2048, ~50 s at n = 4096 and ~5 min at n = 8192 on 8 cores)
 CPU_SAMPLE_N = 2048
 CPU_SAMPLE_GRID = 64
-# DRAM bytes (read + write) of one k_mf_bf16x3 launch from an ncu capture of
-# the current kernel at the workload's size, or None
-MF_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one k_mf_bf16x3<64> launch at n = 65536, d = 64
+# from a one-pass ncu capture of the current kernel (17.09 MB read: the split
+# operands once; 13.70 MB written: partials); profiles/k_mf_bf16x3_n16384_d64.md
+# gives the command.  None for any other workload.
+MF_TRAFFIC_BYTES_C3 = 30.79e6
 SFU_EX2_PER_CLK_PER_SM = 32   # ex2.approx results per clock per SM (micro-benchmarked on GB300)
 FP64_NOMINAL_TFLOPS = 1.25    # dense float64 rate of GB300 (nominal)
 
@@ -292,7 +294,8 @@ def run_ours(args):
                               "column sums) + k_mf_finish",
                     "bound": "tensor" if t_tensor >= t_sfu else "sfu", "achieved": achieved, "peak": bf16_peak,
                     "peak_kind": peak_kind + " bf16 burst (kernel timed alone)", "unit": "TFLOP/s",
-                    "frac": achieved / bf16_peak, "traffic": MF_TRAFFIC_BYTES,
+                    "frac": achieved / bf16_peak,
+                    "traffic": MF_TRAFFIC_BYTES_C3 if (n == 65536 and inst.d == 64) else None,
                     "method_flops_per_product": flops, "unique_pairs": pairs,
                     "ms_per_product": prod_ms, "ms_main_kernel": main_ms,
                     "tensor_roof_ms": t_tensor * 1e3, "sfu_roof_ms": t_sfu * 1e3,
