@@ -152,6 +152,29 @@ class ClockSampler:
 # Our CUDA path
 # ---------------------------------------------------------------------------
 
+def rank_env():
+    """(world size, rank, local rank) of a torchrun launch; (1, 0, 0) without one."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def job_ms(ms: float, world: int, device) -> float:
+    """The job's time for `world` replicas: the slowest rank's, by a MAX
+    all-reduce over the process group (every rank gets it)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -160,9 +183,7 @@ def run_ours(args):
     from paper_2604_25138_gb300 import laker as L
 
     cfg = SINGLE[args.workload]
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -225,13 +246,9 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     launches = ctx.launches() - launches0
     dev_ms = ev0.elapsed_time(ev1)
-    ms = max(dev_ms, wall * 1e3)
-    if world > 1:
-        t = torch.tensor([ms], device=dev_t)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_ms(max(dev_ms, wall * 1e3), world, dev_t)
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_throughput(args.steps, world, ms)
     info, finfo = infos[-1]
     alpha_m, fmap_m = alpha.clone(), fmap.clone()
 
@@ -250,7 +267,7 @@ def run_ours(args):
         out_a.copy_(a, non_blocking=True)
         out_m.copy_(fm, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = job_ms((time.perf_counter() - t0) / e2e_steps * 1e3, world, dev_t) / 1e3
 
     # roofline of the dominant kernel: the matrix-free product.  The method's
     # own work per unique pair (n(n+1)/2 pairs; the operator is symmetric) is
@@ -1042,8 +1059,7 @@ def run_reference(args):
     """The reference arm: the float64 oracle as it stands, on the host cores;
     each step is one whole oracle solve of the bounded sample instance of the
     workload (see oracle_baseline)."""
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = rank_env()
     if rank != 0:
         return
     cfg = SINGLE[args.workload if args.workload in SINGLE else "c3"]
