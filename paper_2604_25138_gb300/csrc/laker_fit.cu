@@ -837,7 +837,9 @@ laker_status fit_cccp(laker_ctx* ctx, const laker_op* op, const double* Z, int n
     }
     // ---- P = Sigma^-1/2 via the eigendecomposition of D^1/2 M D^1/2
     double *Sm = nullptr, *V = nullptr, *cs = nullptr, *X = nullptr, *B0 = nullptr, *B = nullptr, *nrm = nullptr;
-    const int m = NP;   // even
+    // N_r rounded up to even (the round-robin pairing needs an even size; a
+    // zero-padded index still costs a round of every sweep)
+    const int m = (nr + 1) / 2 * 2;
     if ((st = lk_malloc(ctx, (void**)&Sm, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&V, (size_t)m * m * sizeof(double))) != LAKER_OK) return st;
     if ((st = lk_malloc(ctx, (void**)&cs, (size_t)m * sizeof(double))) != LAKER_OK) return st;
