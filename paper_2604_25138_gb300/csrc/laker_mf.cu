@@ -73,7 +73,7 @@ struct MfSmem {
     uint64_t bfull;
     uint64_t bempty;
     uint32_t tmem_base;
-    // column sums of the four epilogue parts of a lane quadrant, by tile parity
+    // column sums of the four epilogue parts of a lane quadrant, two buffers
     float cred[2][4][MF_EPW][32];
 };
 
@@ -316,6 +316,11 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
             const int slot = g - mf_owner(mf_row_start(blk, sch), sch);
             rowpart[(((int64_t)blk * sch.slots + slot) * 4 + q) * MF_B + h * MF_WCOLS + lane] = a[0];
         };
+        // once a bounded wait has expired (the error word is set) a warp skips
+        // its waits and tensor-memory reads but runs on through the tiles, so
+        // that the four warps of a quadrant still meet at every named barrier
+        bool live = true;
+        int noff = 0;   // off-diagonal tiles so far (the same in every warp)
         if (ntiles > 0) load_seg(I0);
         float pj_next = ntiles > 0 ? __ldg(pf + (int64_t)((I0 + k0) % sch.nb) * MF_B + q * 32 + lane) : 0.f;
         for (int it = 0; it < ntiles; ++it) {
@@ -331,25 +336,32 @@ k_mf_bf16x3(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ 
             if (it + 1 < ntiles) pj_next = __ldg(pf + (int64_t)((In + kn) % sch.nb) * MF_B + q * 32 + lane);
             const int accb = it % MF_NACC;
             const uint32_t aph = (it / MF_NACC) & 1;
-            // one lane waits, the warp follows: tcgen05.ld below must run converged
-            int ok = (lane == 0) ? (int)mbar_wait(&S->tfull[accb], aph, err) : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t tcol = tmem + lane_addr + accb * MF_B + h * MF_WCOLS;
+            if (live) {
+                // one lane waits, the warp follows: tcgen05.ld below must run converged
+                const int w = (lane == 0) ? (int)mbar_wait(&S->tfull[accb], aph, err) : 0;
+                live = __shfl_sync(0xffffffffu, w, 0) != 0;
+            }
             float2 sJ[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-            if (diag) mf_tile_epilogue<true>(tcol, acc, pI4, pj, sJ);
-            else mf_tile_epilogue<false>(tcol, acc, pI4, pj, sJ);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S->tempty[accb]);
+            if (live) {
+                tc_fence_after();
+                const uint32_t tcol = tmem + lane_addr + accb * MF_B + h * MF_WCOLS;
+                if (diag) mf_tile_epilogue<true>(tcol, acc, pI4, pj, sJ);
+                else mf_tile_epilogue<false>(tcol, acc, pI4, pj, sJ);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S->tempty[accb]);
+            }
             if (!diag) {
                 const float part = (sJ[0].x + sJ[0].y) + (sJ[1].x + sJ[1].y);
                 if (MfCfg<DPAD>::REDUCE) {
                     // the quadrant's four parts of a column are added in shared
                     // memory, in a fixed order, and written once: a quarter of
-                    // the partial traffic of writing them apart
-                    float(*cr)[32] = S->cred[it & 1][q];
+                    // the partial traffic of writing them apart.  The buffer
+                    // alternates per off-diagonal tile, so that the barrier of
+                    // the tile between two uses of a buffer orders part 0's
+                    // reads before the next writes
+                    float(*cr)[32] = S->cred[noff & 1][q];
+                    ++noff;
                     cr[h][lane] = part;
                     asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(32 * MF_EPW) : "memory");
                     if (h == 0)
