@@ -14,7 +14,8 @@ throughout) is timed on the same instance in the same run, and the line
 reports the mixed alpha's error against it and the dB RMSE of the two maps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c3|c2|batched|learned|sweep]
+                  [--workload n65536_d64|n16384_d32|n1024_fp64|batched|learned|
+                              sweep|variants|combined|streaming]
 
 Multi-GPU: the instance does not shard; N ranks run N independent replicas
 (different seeds), `value` = instances solved by all ranks / max rank time.
@@ -43,11 +44,11 @@ UNIT = "solves/s"
 # single-instance workloads: the precision form (headline) and the larger
 # plain-method instance
 SINGLE = {
-    "c3": dict(name="precision form: single instance, n=65536 uniform, d=64, lambda=1e-4, 8 Tx, 512x512 grid",
+    "n65536_d64": dict(name="precision form: single instance, n=65536 uniform, d=64, lambda=1e-4, 8 Tx, 512x512 grid",
                n=65536, d=64, lam=1e-4, n_tx=8, layout="uniform", grid=512, tol=1e-6, refine_every=20, seed=3000),
-    "c2": dict(name="single instance, n=16384 (70% uniform, 30% in 5 blobs), d=32, lambda=1e-4, 8 Tx, 512x512 grid",
+    "n16384_d32": dict(name="single instance, n=16384 (70% uniform, 30% in 5 blobs), d=32, lambda=1e-4, 8 Tx, 512x512 grid",
                n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6, refine_every=20, seed=2000),
-    "c1": dict(name="plain method in float64: single instance, n=1024 uniform, d=16, lambda=1e-3, 3 Tx, 64x64 grid",
+    "n1024_fp64": dict(name="plain method in float64: single instance, n=1024 uniform, d=16, lambda=1e-3, 3 Tx, 64x64 grid",
                n=1024, d=16, lam=1e-3, n_tx=3, layout="uniform", grid=64, tol=1e-8, refine_every=0, seed=1000,
                precision="FP64"),
 }
@@ -409,8 +410,8 @@ def run_batched(args):
     torch.cuda.set_device(0)
     build.build()
     dev_t = torch.device("cuda", 0)
-    specs = synth.batch_specs(synth.CONFIGS["c4"]["count"], 4000)
-    tol = synth.CONFIGS["c4"]["tol"]
+    specs = synth.batch_specs(synth.CONFIGS["batch256"]["count"], 4000)
+    tol = synth.CONFIGS["batch256"]["tol"]
     ctx = L.Context(0)
 
     def to_dev(x):
@@ -697,7 +698,7 @@ def run_sweep(args):
 
 def run_variants(args):
     """The per-n choice of the float32-class operator: for n from 512 to
-    32768 (d = 32, the c2 field and layout), an FP32 operator built with
+    32768 (d = 32, the field and layout of the n = 16384 instance), an FP32 operator built with
     LAKER_AUTO times one product of the materialised variant (stream of the
     float32 G) and of the matrix-free one (split-bf16 tcgen05 kernel) and keeps
     the faster; the line reports both times, the choice, and the algorithmic
@@ -1062,7 +1063,7 @@ def run_reference(args):
     world, rank, _ = rank_env()
     if rank != 0:
         return
-    cfg = SINGLE[args.workload if args.workload in SINGLE else "c3"]
+    cfg = SINGLE[args.workload if args.workload in SINGLE else "n65536_d64"]
     inst, Z, n_r = workload(cfg, cfg["seed"] + 77, n=CPU_SAMPLE_N, grid=CPU_SAMPLE_GRID)
     for _ in range(args.warmup):
         oracle_solve(inst, Z, n_r, cfg["tol"])
@@ -1098,9 +1099,9 @@ def main():
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[50, 200, 500, 1000, 2000, 4000, 8000])
     ap.add_argument("--gd-steps", type=int, default=2000)
     ap.add_argument("--variant-sizes", type=int, nargs="+", default=[512, 1024, 2048, 4096, 8192, 16384, 32768])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "batched", "learned", "sweep", "variants", "combined", "streaming"],
-                    help="c3: the precision-form instance n=65536, d=64 (the headline line); c2: the n=16384 "
-                         "instance; batched: 256 instances; learned: the set-network preconditioner")
+    ap.add_argument("--workload", default="n65536_d64", choices=["n65536_d64", "n16384_d32", "n1024_fp64", "batched", "learned", "sweep", "variants", "combined", "streaming"],
+                    help="n65536_d64: the precision-form instance (the headline line); n16384_d32: the clustered "
+                         "n=16384 instance; n1024_fp64: the small float64 instance; batched: 256 instances; learned: the set-network preconditioner")
     ap.add_argument("--learned-train", type=int, default=256)
     ap.add_argument("--learned-test", type=int, default=32)
     ap.add_argument("--learned-big", type=int, default=4)

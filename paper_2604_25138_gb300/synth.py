@@ -161,10 +161,10 @@ def default_num_directions(n: int) -> int:
 
 # Configurations of the workloads (sizes and field parameters).
 CONFIGS = {
-    "c1": dict(n=1024, d=16, lam=1e-3, n_tx=3, layout="uniform", grid=64, tol=1e-8),
-    "c2": dict(n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6),
-    "c3": dict(n=65536, d=64, lam=1e-4, n_tx=8, layout="uniform", grid=512, tol=1e-6),
-    "c4": dict(count=256, n_lo=512, n_hi=8192, d_choices=(16, 32), lam_lo=1e-5, lam_hi=1e-2,
+    "n1024_fp64": dict(n=1024, d=16, lam=1e-3, n_tx=3, layout="uniform", grid=64, tol=1e-8),
+    "n16384_d32": dict(n=16384, d=32, lam=1e-4, n_tx=8, layout="clustered", grid=512, tol=1e-6),
+    "n65536_d64": dict(n=65536, d=64, lam=1e-4, n_tx=8, layout="uniform", grid=512, tol=1e-6),
+    "batch256": dict(count=256, n_lo=512, n_hi=8192, d_choices=(16, 32), lam_lo=1e-5, lam_hi=1e-2,
                tx_lo=1, tx_hi=8, f_lo=0.7e9, f_hi=6e9, layout="uniform", tol=1e-6),
 }
 
@@ -174,7 +174,7 @@ def batch_specs(count: int, seed: int, cfg: dict | None = None) -> list:
     [n_lo, n_hi], d uniform over d_choices, lambda log-uniform, 1-8
     transmitters and a carrier frequency uniform in [f_lo, f_hi] (a pure
     offset of the standardised y).  Returns dicts for make_instance."""
-    c = dict(CONFIGS["c4"]) if cfg is None else cfg
+    c = dict(CONFIGS["batch256"]) if cfg is None else cfg
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):

@@ -71,7 +71,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
 
     class Args:
-        workload = "c3"
+        workload = "n65536_d64"
         steps = 1
         warmup = 0
 

@@ -31,7 +31,7 @@ def test_c2_solves_and_map_full_size(L):
         return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
     ctx = L.Context(0)
-    c = synth.CONFIGS["c2"]
+    c = synth.CONFIGS["n16384_d32"]
     inst = synth.make_instance(c["n"], c["d"], c["lam"], n_tx=c["n_tx"], seed=2000, layout=c["layout"],
                                grid=c["grid"])
     n = inst.n

@@ -166,7 +166,7 @@ def test_c1_end_to_end_fp64(L, ctx):
     (summation-order permutations and per-apply noise at the measured
     difference of the GPU's apply) and alpha against the exact solution."""
     from tests.gpu_util import dev, host, rel
-    cfg = synth.CONFIGS["c1"]
+    cfg = synth.CONFIGS["n1024_fp64"]
     inst = synth.make_instance(cfg["n"], cfg["d"], cfg["lam"], n_tx=cfg["n_tx"], seed=1001, grid=cfg["grid"])
     n = inst.n
     n_r = synth.default_num_directions(n)
@@ -439,14 +439,14 @@ def test_auto_variant_keeps_the_faster_product(L, ctx, n):
 
 
 def test_c1_stopping_index_five_seeds(L, ctx):
-    """The c1 configuration (n = 1024, d = 16, lambda = 1e-3, 3 Tx, N_r = 64,
+    """The small float64 workload (n = 1024, d = 16, lambda = 1e-3, 3 Tx, N_r = 64,
     tol 1e-8) on five seeds: the GPU's number of products lies within the
     oracle's own envelope of it (plain run, six summation-order permutations,
     six runs with per-apply noise at the measured difference between the
     GPU's float64 apply and the oracle's dense Sigma^-1/2 r), widened by the
     envelope's width.  Prints the distribution of GPU - oracle."""
     from tests.gpu_util import dev, host, rel
-    cfg = synth.CONFIGS["c1"]
+    cfg = synth.CONFIGS["n1024_fp64"]
     deltas = []
     for seed in (1001, 1002, 1003, 1004, 1005):
         inst = synth.make_instance(cfg["n"], cfg["d"], cfg["lam"], n_tx=cfg["n_tx"], seed=seed, grid=2)

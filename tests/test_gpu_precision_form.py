@@ -40,7 +40,7 @@ def test_precision_form_n8192_against_oracle(L):
     its radio map on sampled grid points is within 0.01 dB of the map of the
     oracle's exact solution."""
     ctx = L.Context(0)
-    c = synth.CONFIGS["c3"]
+    c = synth.CONFIGS["n65536_d64"]
     n = 8192
     inst = synth.make_instance(n, c["d"], c["lam"], n_tx=c["n_tx"], seed=3101, layout=c["layout"], grid=64)
     A = O.system_matrix(inst.Q, inst.scale, inst.lam)
@@ -72,7 +72,7 @@ def test_precision_form_full_size_against_float64_gpu(L):
     difference on 4096 sampled grid points (dB RMSE <= 0.01 dB)."""
     import torch
     ctx = L.Context(0)
-    c = synth.CONFIGS["c3"]
+    c = synth.CONFIGS["n65536_d64"]
     inst = synth.make_instance(c["n"], c["d"], c["lam"], n_tx=c["n_tx"], seed=3003, layout=c["layout"],
                                grid=c["grid"])
     n = inst.n
