@@ -232,7 +232,8 @@ laker_status laker_fit_preconditioner_seeded(laker_ctx* ctx, const laker_op* op,
  * continue prev's: Z is prev's Z with rows appended for the new points (the
  * same n_r columns).  All other arguments, the result and the errors are those
  * of laker_fit_preconditioner; LAKER_ERR_ARG also if prev is not a CCCP
- * preconditioner over n_r directions.
+ * preconditioner over n_r directions, or if op or prev belongs to another
+ * device than ctx.
  */
 laker_status laker_fit_preconditioner_warm(laker_ctx* ctx, const laker_op* op, const double* Z, int n_r,
                                            double gamma, double rho, double eps, int max_iter, double tol,
@@ -465,7 +466,9 @@ laker_status laker_pcg_solve_batched(laker_ctx* ctx, int count, const laker_batc
  * Errors: LAKER_ERR_ARG for bad arguments or a shared workspace operator;
  * LAKER_ERR_NONFINITE for a non-finite y; otherwise the worst instance status
  * (a hard error, then LAKER_ERR_BREAKDOWN, then LAKER_ERR_MAXITER), every
- * alpha written and its info saying which failed.
+ * alpha written and its info saying which failed.  An instance that no worker
+ * thread could run (none could select the device) reports LAKER_ERR_CUDA in
+ * its info.
  */
 laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, const laker_batch_item* items, double tol,
                                         int max_iter, int refine_every, int streams, laker_solve_info* infos,

@@ -331,6 +331,8 @@ laker_status laker_fit_preconditioner_warm(laker_ctx* ctx, const laker_op* op, c
     if (n_r < 1 || n_r > LK_MAX_NR) return set_error(ctx, LAKER_ERR_ARG, "need 1 <= n_r <= 2048");
     if (prev->kind != PRECOND_CCCP || prev->n_r != n_r || !prev->D)
         return set_error(ctx, LAKER_ERR_ARG, "warm start needs a CCCP preconditioner over the same n_r directions");
+    if (prev->device != ctx->device || op->device != ctx->device)
+        return set_error(ctx, LAKER_ERR_ARG, "operator or previous preconditioner belongs to another device");
     if (!(gamma >= 0.0) || !(eps > 0.0) || rho > 1.0 || max_iter < 1 || !(tol >= 0.0))
         return set_error(ctx, LAKER_ERR_ARG, "bad CCCP parameters");
     if ((st = scan_finite(ctx, Z, op->n * (int64_t)n_r)) != LAKER_OK) return st;

@@ -86,10 +86,11 @@ extern "C" laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, co
             st = set_error(ctx, LAKER_ERR_CUDA, "stream wait failed");
     if (st != LAKER_OK) { cleanup(); return st; }
 
-    std::vector<laker_status> status((size_t)count, LAKER_OK);
+    // an instance no worker took (none could select the device) reports an error, not success
+    std::vector<laker_status> status((size_t)count, LAKER_ERR_CUDA);
     std::vector<laker_solve_info> info((size_t)count);
     std::vector<double> done((size_t)count, 0.0);
-    std::vector<std::string> why((size_t)count);
+    std::vector<std::string> why((size_t)count, "not run: no worker thread could select the device");
     std::atomic<int> next{0};
     const auto t0 = std::chrono::steady_clock::now();
     auto worker = [&](int w) {
@@ -100,6 +101,7 @@ extern "C" laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, co
             if (i >= count) break;
             const laker_batch_item& it = items[i];
             laker_solve_info fi{};
+            why[(size_t)i].clear();
             status[(size_t)i] = pcg_solve(&c, it.op, it.P, it.y, it.alpha, tol, max_iter, refine_every, &fi, nullptr,
                                           0, 0.0, 0.0, false, &arena[(size_t)w]);
             if (status[(size_t)i] != LAKER_OK) {
@@ -111,10 +113,16 @@ extern "C" laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, co
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
     };
+    // the threads that started take every instance between them; if none
+    // could be started the calling thread runs worker 0 itself
     std::vector<std::thread> pool;
-    pool.reserve((size_t)streams);
-    for (int w = 0; w < streams; ++w) pool.emplace_back(worker, w);
+    try {
+        pool.reserve((size_t)streams);
+        for (int w = 0; w < streams; ++w) pool.emplace_back(worker, w);
+    } catch (...) {
+    }
     for (std::thread& t : pool) t.join();
+    if (pool.empty()) worker(0);
 
     // the worst status: hard errors, then breakdown, then max_iter
     const auto rank = [](laker_status x) {
@@ -123,7 +131,10 @@ extern "C" laker_status laker_pcg_solve_concurrent(laker_ctx* ctx, int count, co
     laker_status worst = LAKER_OK;
     std::string msg;
     for (int i = 0; i < count; ++i) {
-        if (infos) infos[i] = info[(size_t)i];
+        if (infos) {
+            infos[i] = info[(size_t)i];
+            if (status[(size_t)i] != LAKER_OK) infos[i].status = status[(size_t)i];
+        }
         if (done_ms) done_ms[i] = done[(size_t)i];
         if (rank(status[(size_t)i]) > rank(worst)) {
             worst = status[(size_t)i];
